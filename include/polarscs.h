@@ -1,0 +1,133 @@
+/*
+ * polarscs.h - C ABI of the GB300 (sm_103a) stack decoder for polar codes.
+ *
+ * The method is successive-cancellation stack (SCS) decoding with the fast
+ * simplified nodes and the reduced-memory in-place partial sums of Aurora &
+ * Gross, "Towards Practical Software Stack Decoding of Polar Codes"
+ * (arXiv 1809.03606), Sec. 2.2.5, Sec. 3.3 and Sec. 4.
+ *
+ * Conventions shared by every call:
+ *  - A code PC(N, K) is given by N (a power of two), K information bits and a
+ *    frozen mask of N bytes, 1 = frozen (Sec. 2.1).  With a CRC of crc bits the
+ *    message has K - crc bits; the CRC register (initial value 0, no
+ *    reflection, no final XOR, polynomial 0x07 for crc = 8, 0x1021 for 16,
+ *    0xB2B117 for 24) follows the message MSB first on the last crc
+ *    information positions.  Message bit j sits on the j-th information index
+ *    in increasing order.
+ *  - Codewords are c = u F^{(x)n} with the XOR tree of Fig. encoder
+ *    (non-systematic encoding).
+ *  - Channel LLRs are float32, LLR = ln P(0)/P(1); they must be finite.
+ *  - Device buffers are row-major per frame.  Packed bit buffers are uint32
+ *    words, bit j of a row in word j/32 at bit position j%32 (LSB first).
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Batched calls are asynchronous on that stream; the caller
+ *    owns every buffer and must keep it alive until the stream has passed the
+ *    call.  The library keeps no pointer to caller memory after that.
+ *  - Return values: 0 = OK; > 0 is a per-frame decode status (single-frame
+ *    calls only); < 0 is an error and nothing was launched.
+ *  - Every function is thread-safe.  A plan may be shared between threads
+ *    and streams once created.
+ */
+#ifndef POLARSCS_H
+#define POLARSCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* decode status of one frame (also the int8 entries of a status buffer) */
+#define POLAR_OK 0
+#define POLAR_CRC_FAIL 1 /* no complete path passed the CRC: the first complete
+                            path popped is returned (Sec. 2.2.5, CRC rule) */
+#define POLAR_TIMEOUT 2  /* iteration guard tripped; never expected, output zero */
+
+/* errors */
+#define POLAR_EINVAL (-1) /* bad argument: N not a power of 2 in range, K not in
+                             [1, N], D < 1, L < 1, crc not in {0, 8, 16, 24},
+                             crc >= K, frozen count != N - K, NULL pointer */
+#define POLAR_ENOMEM (-2) /* host or device allocation failed */
+#define POLAR_ECUDA (-3)  /* a CUDA call failed (no device, launch error) */
+#define POLAR_ELIMIT (-4) /* valid code, but beyond the GPU kernel's limits:
+                             N > 8192, D > 64 or L > 255 */
+
+/* Maximum sizes the GPU decoder accepts. */
+#define POLAR_MAX_N_GPU 8192
+#define POLAR_MAX_D_GPU 64
+#define POLAR_MAX_L_GPU 255
+
+/* Opaque decoding plan: the precomputed schedule of Sec. 3.1 (Fig. fsscsch)
+ * plus the tables the kernels need.  Created on the host; its device copy is
+ * made on first use on a GPU. */
+typedef struct polar_plan polar_plan;
+
+/* Frozen mask by Bhattacharyya-parameter construction at a design Eb/N0 in dB
+ * (the paper uses the 5G sequence, Sec. 5, which this library does not ship):
+ * z0 = exp(-(K/N) 10^(dB/10)), an f child gets 2z - z^2, a g child z^2, the K
+ * positions of smallest z are information bits (ties: higher index).  Double
+ * precision, host only.  frozen: out, N bytes (1 = frozen).  Returns 0 or
+ * POLAR_EINVAL (N not a power of 2 in [2, 32768], K not in [1, N]). */
+int polar_construct(int N, int K, float design_snr_db, uint8_t *frozen);
+
+/* Build a plan for PC(N, K) with the given frozen mask (host memory, N bytes,
+ * copied).  fast_nodes != 0 recognises the Rate-0, Rate-1, repetition and SPC
+ * nodes of Sec. 2.2.2 (precedence R-0 > R-1 > REP > SPC, SPC from 4 leaves);
+ * 0 decodes bit by bit (Sec. 2.2.1).  crc in {0, 8, 16, 24}.  *out receives a
+ * plan owned by the caller (free with polar_plan_destroy).  Host only: no GPU
+ * is needed to create or inspect a plan.  Errors: POLAR_EINVAL, POLAR_ENOMEM. */
+int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_nodes, int crc, polar_plan **out);
+
+/* Release a plan and its device copy (synchronous; no call using it may be
+ * in flight).  NULL is ignored. */
+void polar_plan_destroy(polar_plan *plan);
+
+/* The plan's schedule (Fig. fsscsch), host logic.  ops_out receives up to
+ * max_ops triples (op, lambda, phi): op 0 = alpha (Eq. llrcalc, node
+ * (lambda, phi) from its parent), 1 = beta (Eq. bitcalc, odd node (lambda, phi)
+ * into its parent), 2 = R-0, 3 = R-1, 4 = REP, 5 = SPC, 6 = frozen leaf,
+ * 7 = information leaf.  Returns the number of operations, or < 0. */
+int polar_plan_schedule(const polar_plan *plan, int32_t *ops_out, int max_ops);
+
+/* Encode B messages on the GPU (Sec. 2.1; the CRC of the plan is appended).
+ * d_msg: device, [B, ceil((K-crc)/32)] packed message bits.  d_codeword:
+ * device, [B, ceil(N/32)] packed codeword bits.  Asynchronous on stream. */
+int polar_encode_batch(const polar_plan *plan, const uint32_t *d_msg, int B, uint32_t *d_codeword, void *stream);
+
+/* Encode one message (host memory, synchronous): msg holds K - crc bits, one
+ * per byte; codeword receives N bytes.  Runs polar_encode_batch on the
+ * current device. */
+int polar_encode(const uint8_t *msg, int N, int K, const uint8_t *frozen, int crc, uint8_t *codeword);
+
+/* Decode B frames on the GPU with FSSCS-RM (Sec. 2.2.5, Sec. 3.3, Sec. 4):
+ * best-first search over a stack of at most D paths, at most L extensions
+ * per branching node, the CRC of the plan checked on complete paths.
+ *  d_llr    device, [B, N] float32 channel LLRs (Eq. llrcalc, stage n)
+ *  d_info   device out, [B, ceil((K-crc)/32)] packed message bits
+ *  d_pm     device out, [B] float32 final path metric (Eq. PMupd)
+ *  d_status device out, [B] int8 POLAR_OK / POLAR_CRC_FAIL / POLAR_TIMEOUT
+ *  d_stats  device out or NULL, [B, 4] uint32: pops, path switches, counted
+ *           operations (the ALU-roofline convention of the design notes),
+ *           expansions.
+ * Scratch (the in-place beta arrays of stacked paths) is allocated
+ * stream-ordered per call.  Asynchronous on stream; errors are returned
+ * before launch (POLAR_EINVAL, POLAR_ELIMIT) or from the launch
+ * (POLAR_ECUDA, POLAR_ENOMEM). */
+int scs_decode_batch(const polar_plan *plan, const float *d_llr, int B, int D, int L, uint32_t *d_info,
+                     float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream);
+
+/* Decode one frame held in host memory (synchronous), fast nodes on:
+ * llr N floats in, info_out K - crc bytes (one bit per byte) out, *pm_out the
+ * final path metric.  Returns the frame status (>= 0) or an error (< 0). */
+int scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int D, int L, int crc, uint8_t *info_out,
+               float *pm_out);
+
+/* Number of SMs and the library's build architecture string, for reports. */
+int polar_device_info(int *sm_count, int *cc_major, int *cc_minor);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLARSCS_H */

@@ -1,0 +1,236 @@
+"""polarscs: batched SCS decoding of polar codes on GB300 (sm_103a).
+
+Thin ctypes binding of ``include/polarscs.h``: the functions below carry the
+C names and only marshal arguments (tensor pointers, the current CUDA stream,
+output allocation).  Every encode and decode step runs in the CUDA kernels
+of ``csrc/``; there is no CPU fallback -- importing the compute entry points
+without the built library raises.
+
+PyTorch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+POLAR_OK, POLAR_CRC_FAIL, POLAR_TIMEOUT = 0, 1, 2
+POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ELIMIT = -1, -2, -3, -4
+MAX_N_GPU, MAX_D_GPU, MAX_L_GPU = 8192, 64, 255
+OP_NAMES = {0: "alpha", 1: "beta", 2: "R0", 3: "R1", 4: "REP", 5: "SPC", 6: "leaf0", 7: "leaf1"}
+
+EXPORTED = (
+    "polar_construct", "polar_plan_create", "polar_plan_destroy", "polar_plan_schedule", "polar_encode_batch",
+    "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info",
+)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PolarError(RuntimeError):
+    def __init__(self, fn: str, rc: int):
+        names = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT"}
+        super().__init__(f"{fn} failed: {names.get(rc, rc)}")
+        self.rc = rc
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libpolarscs.so (building it first only if asked)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libpolarscs.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        lib = C.CDLL(_build.LIB)
+        vp, i32, f32 = C.c_void_p, C.c_int, C.c_float
+        lib.polar_construct.argtypes = [i32, i32, f32, vp]
+        lib.polar_plan_create.argtypes = [i32, i32, vp, i32, i32, C.POINTER(vp)]
+        lib.polar_plan_destroy.argtypes = [vp]
+        lib.polar_plan_destroy.restype = None
+        lib.polar_plan_schedule.argtypes = [vp, vp, i32]
+        lib.polar_encode_batch.argtypes = [vp, vp, i32, vp, vp]
+        lib.polar_encode.argtypes = [vp, i32, i32, vp, i32, vp]
+        lib.scs_decode_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+        lib.scs_decode.argtypes = [vp, i32, i32, vp, i32, i32, i32, vp, vp]
+        lib.polar_device_info.argtypes = [vp, vp, vp]
+        _lib = lib
+        return lib
+
+
+def _check(fn: str, rc: int) -> int:
+    if rc < 0:
+        raise PolarError(fn, rc)
+    return rc
+
+
+def _np_ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream_ptr(stream) -> C.c_void_p:
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(int(s.cuda_stream))
+
+
+def _dev_ptr(t, dtype, name: str, shape=None):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- host calls
+def polar_construct(N: int, K: int, design_snr_db: float) -> np.ndarray:
+    fr = np.zeros(N, np.uint8)
+    _check("polar_construct", load().polar_construct(N, K, float(design_snr_db), _np_ptr(fr)))
+    return fr
+
+
+class Plan:
+    """Owner of a ``polar_plan*`` (the schedule of Fig. fsscsch plus tables)."""
+
+    def __init__(self, N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0):
+        fr = np.ascontiguousarray(frozen, dtype=np.uint8)
+        if fr.size != N:
+            raise ValueError("frozen mask must have N entries")
+        h = C.c_void_p()
+        _check("polar_plan_create", load().polar_plan_create(N, K, _np_ptr(fr), int(bool(fast_nodes)), crc, C.byref(h)))
+        self._h = h
+        self.N, self.K, self.crc, self.fast = N, K, crc, bool(fast_nodes)
+        self.kmsg = K - crc
+        self.frozen = fr.copy()
+        self.words = max(1, N // 32)
+        self.msg_words = (self.kmsg + 31) // 32
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def schedule(self) -> list[tuple[str, int, int]]:
+        return polar_plan_schedule(self)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            load().polar_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def polar_plan_create(N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0) -> Plan:
+    return Plan(N, K, frozen, fast_nodes, crc)
+
+
+def polar_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def polar_plan_schedule(plan: Plan) -> list[tuple[str, int, int]]:
+    n = _check("polar_plan_schedule", load().polar_plan_schedule(plan.handle, None, 0))
+    buf = np.zeros(3 * max(n, 1), np.int32)
+    _check("polar_plan_schedule", load().polar_plan_schedule(plan.handle, _np_ptr(buf), n))
+    t = buf[: 3 * n].reshape(n, 3)
+    return [(OP_NAMES[int(a)], int(b), int(c)) for a, b, c in t]
+
+
+# -------------------------------------------------------------- GPU calls
+def polar_encode_batch(plan: Plan, msg_words, codeword_words, stream=None) -> None:
+    """Encode B packed messages [B, ceil(kmsg/32)] int32 into packed codewords [B, N/32]."""
+    import torch
+
+    B = msg_words.shape[0]
+    _check("polar_encode_batch", load().polar_encode_batch(
+        plan.handle, _dev_ptr(msg_words, torch.int32, "msg_words", (B, plan.msg_words)), B,
+        _dev_ptr(codeword_words, torch.int32, "codeword_words", (B, plan.words)), _stream_ptr(stream)))
+
+
+def polar_encode(msg: np.ndarray, N: int, K: int, frozen: np.ndarray, crc: int = 0) -> np.ndarray:
+    m = np.ascontiguousarray(msg, dtype=np.uint8)
+    fr = np.ascontiguousarray(frozen, dtype=np.uint8)
+    cw = np.zeros(N, np.uint8)
+    _check("polar_encode", load().polar_encode(_np_ptr(m), N, K, _np_ptr(fr), crc, _np_ptr(cw)))
+    return cw
+
+
+def scs_decode_batch(plan: Plan, llr, D: int, L: int, info_words, pm, status, stats=None, stream=None) -> None:
+    """Decode B frames of float32 LLRs [B, N] (CUDA tensors) into the given outputs."""
+    import torch
+
+    B = llr.shape[0]
+    _check("scs_decode_batch", load().scs_decode_batch(
+        plan.handle, _dev_ptr(llr, torch.float32, "llr", (B, plan.N)), B, D, L,
+        _dev_ptr(info_words, torch.int32, "info_words", (B, plan.msg_words)),
+        _dev_ptr(pm, torch.float32, "pm", (B,)), _dev_ptr(status, torch.int8, "status", (B,)),
+        None if stats is None else _dev_ptr(stats, torch.int32, "stats", (B, 4)), _stream_ptr(stream)))
+
+
+def decode(plan: Plan, llr, D: int, L: int, with_stats: bool = False, stream=None):
+    """Allocate outputs and call scs_decode_batch.  Returns (info_words, pm, status[, stats])."""
+    import torch
+
+    B = llr.shape[0]
+    dev = llr.device
+    info = torch.empty((B, plan.msg_words), dtype=torch.int32, device=dev)
+    pm = torch.empty(B, dtype=torch.float32, device=dev)
+    status = torch.empty(B, dtype=torch.int8, device=dev)
+    stats = torch.empty((B, 4), dtype=torch.int32, device=dev) if with_stats else None
+    scs_decode_batch(plan, llr, D, L, info, pm, status, stats, stream)
+    return (info, pm, status, stats) if with_stats else (info, pm, status)
+
+
+def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, D: int, L: int, crc: int = 0):
+    """One frame from host memory (synchronous).  Returns (status, message bits, pm)."""
+    x = np.ascontiguousarray(llr, dtype=np.float32)
+    fr = np.ascontiguousarray(frozen, dtype=np.uint8)
+    out = np.zeros(K - crc, np.uint8)
+    pm = C.c_float(0.0)
+    rc = _check("scs_decode", load().scs_decode(_np_ptr(x), N, K, _np_ptr(fr), D, L, crc, _np_ptr(out), C.byref(pm)))
+    return rc, out, np.float32(pm.value)
+
+
+def polar_device_info() -> dict:
+    sm, ma, mi = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check("polar_device_info", load().polar_device_info(C.byref(sm), C.byref(ma), C.byref(mi)))
+    return dict(sm_count=sm.value, cc=(ma.value, mi.value))
+
+
+# ------------------------------------------------------- bit packing helpers
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """[B, k] 0/1 bytes -> [B, ceil(k/32)] int32 words, bit j in word j/32 at j%32."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    B, k = bits.shape
+    w = (k + 31) // 32
+    pad = np.zeros((B, w * 32), np.uint8)
+    pad[:, :k] = bits
+    return np.packbits(pad, axis=1, bitorder="little").view(np.uint32).astype(np.uint32).view(np.int32).reshape(B, w)
+
+
+def unpack_bits(words: np.ndarray, k: int) -> np.ndarray:
+    """Inverse of pack_bits: [B, w] int32/uint32 words -> [B, k] 0/1 bytes."""
+    words = np.ascontiguousarray(words).view(np.uint32)
+    B = words.shape[0]
+    by = words.reshape(B, -1).view(np.uint8)
+    return np.unpackbits(by, axis=1, bitorder="little")[:, :k]

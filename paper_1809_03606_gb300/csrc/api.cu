@@ -1,0 +1,179 @@
+// api.cu - the C ABI of polarscs.h: argument checks, device copies of plans,
+// and the host-pointer convenience calls.  Every decode and encode step runs
+// in the kernels of scs_decode.cu and encode.cu; nothing here computes on
+// the host except argument validation and table building.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "plan.h"
+
+namespace polarscs {
+
+int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *d_llr, int B, int D, int L,
+                      uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream);
+int launch_polar_encode(const polar_plan *p, const DeviceTables *dt, const uint32_t *d_msg, int B, uint32_t *d_cw,
+                        cudaStream_t stream);
+
+int cuda_status(int err) {
+    const cudaError_t e = cudaError_t(err);
+    if (e == cudaSuccess) return 0;
+    cudaGetLastError();  // clear a sticky non-fatal error state
+    return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
+}
+
+template <typename T>
+static cudaError_t upload(T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), src.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static void free_tables(DeviceTables &d) {
+    cudaFree(d.ops);
+    cudaFree(d.crc_rows);
+    cudaFree(d.msg_pos);
+    cudaFree(d.info_pos);
+    cudaFree(d.crc_contrib);
+    d = DeviceTables{};
+}
+
+int plan_device(const polar_plan *p, const DeviceTables **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::lock_guard<std::mutex> g(p->mu);
+    if (p->dev.device == dev) {
+        *out = &p->dev;
+        return 0;
+    }
+    if (p->dev.device >= 0) return POLAR_EINVAL;  // a plan serves one device
+    DeviceTables d{};
+    d.device = dev;
+    e = upload(&d.ops, p->ops);
+    if (e == cudaSuccess) e = upload(&d.crc_rows, p->crc_rows);
+    if (e == cudaSuccess) e = upload(&d.msg_pos, p->msg_pos);
+    if (e == cudaSuccess) e = upload(&d.info_pos, p->info_pos);
+    if (e == cudaSuccess) e = upload(&d.crc_contrib, p->crc_contrib);
+    if (e != cudaSuccess) {
+        free_tables(d);
+        return cuda_status(e);
+    }
+    p->dev = d;
+    *out = &p->dev;
+    return 0;
+}
+
+}  // namespace polarscs
+
+using namespace polarscs;
+
+extern "C" void polar_plan_destroy(polar_plan *p) {
+    if (!p) return;
+    if (p->dev.device >= 0) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        cudaSetDevice(p->dev.device);
+        free_tables(p->dev);
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    delete p;
+}
+
+extern "C" int scs_decode_batch(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
+                                float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream) {
+    if (!p || B < 0 || D < 1 || L < 1) return POLAR_EINVAL;
+    if (B > 0 && (!d_llr || !d_info || !d_pm || !d_status)) return POLAR_EINVAL;
+    if (p->N > POLAR_MAX_N_GPU || D > POLAR_MAX_D_GPU || L > POLAR_MAX_L_GPU) return POLAR_ELIMIT;
+    if (B == 0) return 0;
+    const DeviceTables *dt = nullptr;
+    int rc = plan_device(p, &dt);
+    if (rc) return rc;
+    return launch_scs_decode(p, dt, d_llr, B, D, L, d_info, d_pm, d_status, d_stats, cudaStream_t(stream));
+}
+
+extern "C" int polar_encode_batch(const polar_plan *p, const uint32_t *d_msg, int B, uint32_t *d_codeword,
+                                  void *stream) {
+    if (!p || B < 0) return POLAR_EINVAL;
+    if (B > 0 && (!d_msg || !d_codeword)) return POLAR_EINVAL;
+    if (B == 0) return 0;
+    const DeviceTables *dt = nullptr;
+    int rc = plan_device(p, &dt);
+    if (rc) return rc;
+    return launch_polar_encode(p, dt, d_msg, B, d_codeword, cudaStream_t(stream));
+}
+
+extern "C" int polar_encode(const uint8_t *msg, int N, int K, const uint8_t *frozen, int crc, uint8_t *codeword) {
+    if (!msg || !frozen || !codeword) return POLAR_EINVAL;
+    polar_plan *p = nullptr;
+    int rc = polar_plan_create(N, K, frozen, 0, crc, &p);
+    if (rc) return rc;
+    const int mw = (p->Kmsg + 31) / 32;
+    std::vector<uint32_t> hm(static_cast<size_t>(mw), 0u), hc(static_cast<size_t>(p->W), 0u);
+    for (int j = 0; j < p->Kmsg; ++j)
+        if (msg[j] & 1) hm[size_t(j >> 5)] |= 1u << (j & 31);
+    uint32_t *dm = nullptr, *dc = nullptr;
+    cudaError_t e = cudaMalloc(&dm, hm.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dc, hc.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(dm, hm.data(), hm.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        rc = polar_encode_batch(p, dm, 1, dc, nullptr);
+        if (rc == 0) e = cudaMemcpy(hc.data(), dc, hc.size() * 4, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(dm);
+    cudaFree(dc);
+    polar_plan_destroy(p);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (rc) return rc;
+    for (int i = 0; i < N; ++i) codeword[i] = uint8_t((hc[size_t(i >> 5)] >> (i & 31)) & 1u);
+    return 0;
+}
+
+extern "C" int scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int D, int L, int crc,
+                          uint8_t *info_out, float *pm_out) {
+    if (!llr || !frozen || !info_out || !pm_out) return POLAR_EINVAL;
+    polar_plan *p = nullptr;
+    int rc = polar_plan_create(N, K, frozen, 1, crc, &p);
+    if (rc) return rc;
+    const int iw = (p->Kmsg + 31) / 32;
+    float *dl = nullptr, *dpm = nullptr;
+    uint32_t *di = nullptr;
+    int8_t *dst = nullptr;
+    std::vector<uint32_t> hi(size_t(iw), 0u);
+    int8_t status = 0;
+    cudaError_t e = cudaMalloc(&dl, size_t(N) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&di, size_t(iw) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dpm, 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dst, 1);
+    if (e == cudaSuccess) e = cudaMemcpy(dl, llr, size_t(N) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        rc = scs_decode_batch(p, dl, 1, D, L, di, dpm, dst, nullptr, nullptr);
+        if (rc == 0) e = cudaMemcpy(hi.data(), di, size_t(iw) * 4, cudaMemcpyDeviceToHost);
+        if (rc == 0 && e == cudaSuccess) e = cudaMemcpy(pm_out, dpm, 4, cudaMemcpyDeviceToHost);
+        if (rc == 0 && e == cudaSuccess) e = cudaMemcpy(&status, dst, 1, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(dl);
+    cudaFree(di);
+    cudaFree(dpm);
+    cudaFree(dst);
+    const int kmsg = p->Kmsg;
+    polar_plan_destroy(p);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (rc) return rc;
+    for (int j = 0; j < kmsg; ++j) info_out[j] = uint8_t((hi[size_t(j >> 5)] >> (j & 31)) & 1u);
+    return int(status);
+}
+
+extern "C" int polar_device_info(int *sm_count, int *cc_major, int *cc_minor) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (sm_count) cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (cc_major) cudaDeviceGetAttribute(cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (cc_minor) cudaDeviceGetAttribute(cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return 0;
+}

@@ -1,0 +1,73 @@
+// plan.h - internal plan representation shared by the library's translation
+// units (host builder, kernels, C ABI).  Not part of the public interface.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "polarscs.h"
+
+namespace polarscs {
+
+// Kernel operation codes.  alpha ops of Eq. llrcalc are split into F (even
+// child, min-sum f) and G (odd child, g); COMB is the in-place beta operation
+// of Sec. 4.  Codes >= OP_BRANCH create several candidate paths.
+enum OpCode : uint32_t {
+    OP_F = 0,
+    OP_G = 1,
+    OP_COMB = 2,
+    OP_R0 = 3,
+    OP_LEAF0 = 4,
+    OP_LEAF1 = 5,  // first branching code
+    OP_REP = 6,
+    OP_R1 = 7,
+    OP_SPC = 8,
+};
+constexpr uint32_t OP_BRANCH = OP_LEAF1;
+constexpr uint32_t NO_TARGET = 0xFFFFFFFFu;
+
+// One schedule entry, 16 bytes, read by every lane of a warp (broadcast).
+//  x: code | lambda << 8      (lambda of the node the op writes / decodes)
+//  y: first leaf s of that node
+//  z: alpha restore target for a path resuming at this op: the node whose
+//     alpha the next alpha-reading op needs, as lambda | s << 8, or NO_TARGET
+//  w: branching ordinal (index of the visit counter) for codes >= OP_BRANCH
+struct alignas(16) KOp {
+    uint32_t x, y, z, w;
+};
+
+struct DeviceTables {
+    int device = -1;
+    KOp *ops = nullptr;
+    uint32_t *crc_rows = nullptr;    // crc x W words: syndrome bit r over codeword bits
+    uint16_t *msg_pos = nullptr;     // Kmsg information indices of the message bits
+    uint16_t *info_pos = nullptr;    // K information indices
+    uint32_t *crc_contrib = nullptr; // Kmsg CRC registers of unit messages
+};
+
+}  // namespace polarscs
+
+struct polar_plan {
+    int N = 0, n = 0, K = 0, Kmsg = 0, crc = 0, fast = 0;
+    int W = 0;        // 32-bit words of a packed N-bit array (at least 1)
+    int nbranch = 0;  // branching operations (visit counters)
+    std::vector<uint8_t> frozen;
+    std::vector<polarscs::KOp> ops;
+    std::vector<uint32_t> crc_rows;
+    std::vector<uint16_t> msg_pos, info_pos;
+    std::vector<uint32_t> crc_contrib;
+    mutable std::mutex mu;
+    mutable polarscs::DeviceTables dev;
+};
+
+namespace polarscs {
+
+int validate_code(int N, int K, const uint8_t *frozen, int crc);
+uint32_t crc_polynomial(int crc);
+// Upload the plan's tables to the current device (once).  Returns 0 or an error.
+int plan_device(const polar_plan *plan, const DeviceTables **out);
+int cuda_status(int err);  // map a cudaError_t to POLAR_ECUDA / POLAR_ENOMEM
+
+}  // namespace polarscs

@@ -1,0 +1,783 @@
+// scs_decode.cu - FSSCS-RM stack decoding of many independent frames on
+// sm_103a (Sec. 2.2.5 SCS, Sec. 3.3 reduced memory, Sec. 4 fast simplified
+// stack decoding).
+//
+// GB300 mapping
+//  - One warp decodes one frame; warps are persistent and claim frames from
+//    a global counter, so frames of very different cost (path switches grow
+//    at low SNR) balance across the 152 SMs.
+//  - Per warp, shared memory holds the single alpha tree of the reduced-
+//    memory scheme (stage lambda at float offset 2^lambda, the root stays in
+//    global memory and is read through L2), the in-place N-bit beta array
+//    (packed 32 bits per word) and the per-node visit counters.
+//  - The stack (D <= 64 entries) lives in registers, two entries per lane:
+//    path metric bits, length|schedule position, sequence number and a
+//    reference to a beta snapshot plus a flip mask.  Pop, worst-entry search
+//    and the L-prune are warp reductions (redux.sync).
+//  - Each branching node writes ONE snapshot of the beta array (the hard
+//    decisions of the node in place) to scratch global memory; its 2-8
+//    candidates differ from it by flips of at most 4 positions (or all
+//    positions for REP), so a candidate costs registers only.  Snapshots are
+//    read back only on a path switch, after which the alpha spine is
+//    recomputed from the channel LLRs (Alg. calp).
+//  - All arithmetic on alpha and path metrics is float32 add/min/compare in
+//    the order of the reference definitions (no FMA: nothing here multiplies).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan.h"
+
+namespace polarscs {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;  // path-metric bits of an empty slot
+constexpr uint32_t NOSNAP = 0xFFu;       // snapshot id of the initial path
+constexpr uint32_t FLIP_ALL = 16u;       // REP second candidate: flip every bit
+
+struct Args {
+    const float *llr;
+    int B, N, n, W, Kmsg, crc, D, L;
+    const KOp *ops;
+    int nops, nbranch;
+    const uint32_t *crc_rows;
+    const uint16_t *msg_pos;
+    uint32_t *info_out;
+    int info_words;
+    float *pm_out;
+    int8_t *status_out;
+    uint32_t *stats_out;
+    uint32_t *scratch;
+    int snap_words;  // words per snapshot slot: W beta words + 4 meta words, padded
+    unsigned *counter;
+    int max_iter;
+    uint32_t stack_cost;
+    int warp_smem;  // bytes of shared memory per warp
+};
+
+__device__ __forceinline__ float f_minsum(float a, float b) {
+    // Eq. minsum: sign(a) sign(b) min(|a|, |b|); the sign bit is the XOR of
+    // the operands' sign bits
+    const float m = fminf(fabsf(a), fabsf(b));
+    const uint32_t sg = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
+    return __uint_as_float(__float_as_uint(m) | sg);
+}
+
+__device__ __forceinline__ float g_op(float a, float b, uint32_t bit) {
+    // Eq. minsum / Fig. minsum: g = b + (1 - 2 beta) a, a = alpha_p[i],
+    // b = alpha_p[i + Lambda]
+    return bit ? __fsub_rn(b, a) : __fadd_rn(b, a);
+}
+
+__device__ __forceinline__ float pen_transform(float x, int mode) {
+    // 0: x; 1: |x| where HD(x) = 1 (disagrees with 0); 2: |x| where HD(x) = 0
+    if (mode == 0) return x;
+    const bool neg = x < 0.0f;
+    return (mode == 1) == neg ? fabsf(x) : 0.0f;
+}
+
+struct Warp {
+    const Args &a;
+    const int lane;
+    float *alpha;     // shared: stage lambda at alpha + 2^lambda
+    uint32_t *beta;   // shared: W words
+    uint8_t *cnt;     // shared: visit counters
+    uint32_t *scr;    // global: (D + 1) snapshot slots
+    const float *root;
+
+    __device__ const float *stage(int lam) const { return lam == a.n ? root : alpha + (1 << lam); }
+
+    // alpha of the even child (lamc, sc) from its parent (Eq. llrcalc, f)
+    __device__ void op_f(int lamc) const {
+        const int len = 1 << lamc;
+        const float *P = stage(lamc + 1);
+        float *C = alpha + len;
+        for (int i = lane; i < len; i += 32) C[i] = f_minsum(P[i], P[i + len]);
+        __syncwarp();
+    }
+
+    // alpha of the odd child (lamc, sc) from its parent and the left
+    // sibling's bits beta[sc - 2^lamc, sc) (Eq. llrcalc, g)
+    __device__ void op_g(int lamc, int sc) const {
+        const int len = 1 << lamc;
+        const int sl = sc - len;
+        const float *P = stage(lamc + 1);
+        float *C = alpha + len;
+        for (int i = lane; i < len; i += 32) {
+            const int pos = sl + i;
+            const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
+            C[i] = g_op(P[i], P[i + len], bit);
+        }
+        __syncwarp();
+    }
+
+    // in-place beta operation of Sec. 4: beta[sl + i] ^= beta[sr + i]
+    __device__ void op_comb(int lamc, int sr) const {
+        const int len = 1 << lamc;
+        const int sl = sr - len;
+        if (len >= 32) {
+            const int wl = sl >> 5, wr = sr >> 5, nw = len >> 5;
+            for (int k = lane; k < nw; k += 32) beta[wl + k] ^= beta[wr + k];
+        } else if (lane == 0) {
+            const int w = sl >> 5, off = sl & 31;
+            const uint32_t v = beta[w];
+            const uint32_t mask = ((1u << len) - 1u) << off;
+            beta[w] = v ^ ((v >> len) & mask);
+        }
+        __syncwarp();
+    }
+
+    // set beta[s, s + 2^lam) to all-zero or all-one
+    __device__ void set_range(int lam, int s, uint32_t bit) const {
+        const int len = 1 << lam;
+        if (len >= 32) {
+            const uint32_t v = bit ? FULL : 0u;
+            for (int k = lane; k < (len >> 5); k += 32) beta[(s >> 5) + k] = v;
+        } else if (lane == 0) {
+            const uint32_t mask = ((1u << len) - 1u) << (s & 31);
+            const uint32_t w = beta[s >> 5];
+            beta[s >> 5] = bit ? (w | mask) : (w & ~mask);
+        }
+        __syncwarp();
+    }
+
+    // hard decisions of the node's alpha into beta[s, s + 2^lam); returns
+    // their parity (XOR)
+    __device__ uint32_t write_hd(const float *A, int lam, int s) const {
+        const int len = 1 << lam;
+        uint32_t par = 0;
+        if (len >= 32) {
+            for (int c = 0; c < (len >> 5); ++c) {
+                const uint32_t bits = __ballot_sync(FULL, A[c * 32 + lane] < 0.0f);
+                par ^= __popc(bits) & 1u;
+                if (lane == 0) beta[(s >> 5) + c] = bits;
+            }
+        } else {
+            const uint32_t bits = __ballot_sync(FULL, lane < len && A[lane] < 0.0f);
+            par = __popc(bits) & 1u;
+            if (lane == 0) {
+                const uint32_t mask = ((1u << len) - 1u) << (s & 31);
+                beta[s >> 5] = (beta[s >> 5] & ~mask) | (bits << (s & 31));
+            }
+        }
+        __syncwarp();
+        return par;
+    }
+
+    // sum over the node's 2^lam alpha values (transformed) in halving order:
+    // v[i] += v[i + h], h = 2^(lam-1) ... 1.  Levels wider than a warp are
+    // written into the free alpha stages below the node.
+    __device__ float halving_sum(const float *A, int lam, int mode) const {
+        const int len = 1 << lam;
+        if (len <= 32) {
+            float v = lane < len ? pen_transform(A[lane], mode) : 0.0f;
+            for (int h = len >> 1; h >= 1; h >>= 1) {
+                const float o = __shfl_down_sync(FULL, v, h);
+                if (lane < h) v = __fadd_rn(v, o);
+            }
+            return __shfl_sync(FULL, v, 0);
+        }
+        int h = len >> 1;
+        float *dst = alpha + h;
+        for (int i = lane; i < h; i += 32) dst[i] = __fadd_rn(pen_transform(A[i], mode), pen_transform(A[i + h], mode));
+        __syncwarp();
+        const float *src = dst;
+        while (h > 32) {
+            h >>= 1;
+            float *d2 = alpha + h;
+            for (int i = lane; i < h; i += 32) d2[i] = __fadd_rn(src[i], src[i + h]);
+            __syncwarp();
+            src = d2;
+        }
+        float v = src[lane];
+        __syncwarp();
+        for (int k = 16; k >= 1; k >>= 1) {
+            const float o = __shfl_down_sync(FULL, v, k);
+            if (lane < k) v = __fadd_rn(v, o);
+        }
+        return __shfl_sync(FULL, v, 0);
+    }
+
+    // the k least reliable positions (|alpha|, ties to the lower index)
+    __device__ void least_k(const float *A, int lam, int k, int *m, float *mag) const {
+        const int len = 1 << lam;
+        for (int j = 0; j < k; ++j) {
+            uint32_t bv = EMPTY, bi = EMPTY;
+            for (int i = lane; i < len; i += 32) {
+                bool used = false;
+                for (int q = 0; q < j; ++q) used |= (m[q] == i);
+                if (used) continue;
+                const uint32_t v = __float_as_uint(fabsf(A[i]));
+                if (v < bv) {
+                    bv = v;
+                    bi = uint32_t(i);
+                }
+            }
+            const uint32_t gv = __reduce_min_sync(FULL, bv);
+            const uint32_t gi = __reduce_min_sync(FULL, bv == gv ? bi : EMPTY);
+            m[j] = int(gi);
+            mag[j] = __uint_as_float(gv);
+        }
+    }
+
+    // flip the candidate's positions relative to the node's hard decisions
+    __device__ void apply_flips(uint32_t mask, const int *m, int s, int lam) const {
+        if (mask & FLIP_ALL) {
+            const int len = 1 << lam;
+            if (len >= 32) {
+                for (int k = lane; k < (len >> 5); k += 32) beta[(s >> 5) + k] ^= FULL;
+            } else if (lane == 0) {
+                beta[s >> 5] ^= ((1u << len) - 1u) << (s & 31);
+            }
+        }
+        if (lane == 0) {
+            for (int j = 0; j < 4; ++j)
+                if ((mask >> j) & 1u) {
+                    const int pos = s + m[j];
+                    beta[pos >> 5] ^= 1u << (pos & 31);
+                }
+        }
+        __syncwarp();
+    }
+};
+
+struct Stack {
+    uint32_t pm[2], meta[2], seq[2], aux[2];  // meta = len | sched << 16
+};
+
+__device__ __forceinline__ bool slot_exists(int j, int lane, int D) { return j * 32 + lane < D; }
+
+__device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
+    const int lane = w.lane;
+    const int N = a.N, W = a.W, D = a.D, n = a.n;
+    const int SW = a.snap_words;
+
+    for (int i = lane; i < a.nbranch; i += 32) w.cnt[i] = 0;
+    for (int i = lane; i < W; i += 32) w.beta[i] = 0u;
+    __syncwarp();
+
+    Stack st;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        st.pm[j] = EMPTY;
+        st.meta[j] = 0u;
+        st.seq[j] = 0u;
+        st.aux[j] = NOSNAP;
+    }
+    if (lane == 0) {  // the initial path: pm 0, length 0, schedule 0
+        st.pm[0] = __float_as_uint(0.0f);
+        st.meta[0] = 0u;
+        st.seq[0] = 0u;
+        st.aux[0] = NOSNAP;
+    }
+    int count = 1;
+    uint32_t seq_next = 1;
+    uint32_t ops = a.stack_cost;  // counted operations (roofline convention)
+    uint32_t n_iter = 0, n_switch = 0, n_exp = 0;
+
+    uint32_t cur_snap = NOSNAP;  // snapshot of the latest expansion
+    bool beta_dirty = false;     // working beta replaced since that expansion
+    uint32_t applied = 0;        // flips applied on top of the latest snapshot
+    int cm[4] = {0, 0, 0, 0};
+    int cs = 0, clam = 0;
+
+    int crc_fails = 0;
+    bool have_first = false;
+    float first_pm = 0.0f;
+    int status = POLAR_TIMEOUT;
+    float out_pm = __int_as_float(0x7f800000);
+    int out_src = 0;  // 0: zeros, 1: working beta, 2: first complete path
+
+    // insert one candidate under the stack rules (reading R11)
+    auto insert = [&](uint32_t pmb, uint32_t meta, uint32_t seq, uint32_t aux) {
+        ops += a.stack_cost;
+        if (count < D) {
+            int j = 0;
+            uint32_t bal = __ballot_sync(FULL, st.pm[0] == EMPTY && slot_exists(0, lane, D));
+            if (bal == 0u) {
+                j = 1;
+                bal = __ballot_sync(FULL, st.pm[1] == EMPTY && slot_exists(1, lane, D));
+            }
+            const int l = __ffs(bal) - 1;
+            if (lane == l) {
+                st.pm[j] = pmb;
+                st.meta[j] = meta;
+                st.seq[j] = seq;
+                st.aux[j] = aux;
+            }
+            ++count;
+        } else {
+            // worst = largest pm, ties: oldest (smallest seq)
+            uint32_t k0 = slot_exists(0, lane, D) ? st.pm[0] : 0u;
+            uint32_t k1 = slot_exists(1, lane, D) ? st.pm[1] : 0u;
+            uint32_t lw = k0, ls = st.seq[0];
+            int lj = 0;
+            if (k1 > lw || (k1 == lw && slot_exists(1, lane, D) && st.seq[1] < ls)) {
+                lw = k1;
+                ls = st.seq[1];
+                lj = 1;
+            }
+            if (!slot_exists(0, lane, D) && !slot_exists(1, lane, D)) {
+                lw = 0u;
+                ls = EMPTY;
+            }
+            const uint32_t gw = __reduce_max_sync(FULL, lw);
+            const uint32_t gs = __reduce_min_sync(FULL, lw == gw ? ls : EMPTY);
+            if (pmb < gw) {  // strictly better than the worst: replace it
+                const uint32_t bal = __ballot_sync(FULL, lw == gw && ls == gs);
+                const int l = __ffs(bal) - 1;
+                if (lane == l) {
+                    st.pm[lj] = pmb;
+                    st.meta[lj] = meta;
+                    st.seq[lj] = seq;
+                    st.aux[lj] = aux;
+                }
+            }
+        }
+    };
+
+    // a free snapshot slot among 0 .. D-1 (one always exists: the extended
+    // path left the stack, so at most D - 1 snapshots are referenced)
+    auto alloc_snapshot = [&]() -> int {
+        uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (st.pm[j] != EMPTY) {
+                const uint32_t sn = st.aux[j] & 0xFFu;
+                if (sn < 32u) lo |= 1u << sn;
+                else if (sn < 64u) hi |= 1u << (sn - 32u);
+            }
+        }
+        lo = __reduce_or_sync(FULL, lo);
+        hi = __reduce_or_sync(FULL, hi);
+        uint64_t used = (uint64_t(hi) << 32) | uint64_t(lo);
+        const uint64_t all = (D >= 64) ? ~0ull : ((1ull << D) - 1ull);
+        const uint64_t fr = ~used & all;
+        return fr ? (__ffsll((long long)fr) - 1) : -1;
+    };
+
+    auto write_snapshot = [&](int slot, int nbits, uint32_t m01, uint32_t m23, int s, int lam) {
+        uint32_t *sp = w.scr + size_t(slot) * SW;
+        const int nw = min(W, (nbits + 31) >> 5);
+        for (int k = lane; k < nw; k += 32) sp[k] = w.beta[k];
+        if (lane == 0) {
+            sp[W] = m01;
+            sp[W + 1] = m23;
+            sp[W + 2] = uint32_t(s);
+            sp[W + 3] = uint32_t(lam);
+        }
+    };
+
+    int iter = 0;
+    for (; iter < a.max_iter; ++iter) {
+        if (count == 0) {  // every path deleted (reading R12)
+            status = POLAR_CRC_FAIL;
+            if (have_first) {
+                out_pm = first_pm;
+                out_src = 2;
+            }
+            break;
+        }
+        // ---- pop the best path: smallest pm, ties to the newest ----
+        uint32_t lp = st.pm[0], ls = st.seq[0];
+        int lj = 0;
+        if (D > 32 && (st.pm[1] < lp || (st.pm[1] == lp && st.pm[1] != EMPTY && st.seq[1] > ls))) {
+            lp = st.pm[1];
+            ls = st.seq[1];
+            lj = 1;
+        }
+        const uint32_t gp = __reduce_min_sync(FULL, lp);
+        if (gp == EMPTY) {  // count out of step with the slots: stop safely
+            status = POLAR_TIMEOUT;
+            break;
+        }
+        const uint32_t gs = __reduce_max_sync(FULL, lp == gp ? ls : 0u);
+        const uint32_t bal = __ballot_sync(FULL, lp == gp && ls == gs);
+        const int wl = __ffs(bal) - 1;
+        const int wj = __shfl_sync(FULL, lj, wl);
+        const uint32_t p_pmb = gp;
+        const uint32_t p_meta = __shfl_sync(FULL, wj ? st.meta[1] : st.meta[0], wl);
+        const uint32_t p_aux = __shfl_sync(FULL, wj ? st.aux[1] : st.aux[0], wl);
+        if (lane == wl) {
+            if (wj) st.pm[1] = EMPTY;
+            else st.pm[0] = EMPTY;
+        }
+        --count;
+        ++n_iter;
+        ops += a.stack_cost;
+        const int p_len = int(p_meta & 0xFFFFu);
+        const int p_sched = int(p_meta >> 16);
+        const uint32_t p_snap = p_aux & 0xFFu;
+        const uint32_t p_mask = (p_aux >> 8) & 0x1Fu;
+        (void)p_len;
+        if (p_snap != NOSNAP && p_snap >= uint32_t(D)) {  // never produced; guards the scratch index
+            status = POLAR_TIMEOUT;
+            break;
+        }
+        if (p_sched > a.nops) {
+            status = POLAR_TIMEOUT;
+            break;
+        }
+
+        // ---- restore the path's beta array ----
+        bool need_restore = false;
+        if (p_snap == cur_snap) {
+            if (beta_dirty) {
+                const uint32_t *sp = w.scr + size_t(cur_snap) * SW;
+                for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
+                __syncwarp();
+                applied = 0u;
+                beta_dirty = false;
+            }
+            w.apply_flips(applied ^ p_mask, cm, cs, clam);
+            applied = p_mask;
+        } else {  // path switch (Sec. 3.3)
+            ++n_switch;
+            ops += uint32_t(W);
+            const uint32_t *sp = w.scr + size_t(p_snap) * SW;
+            for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
+            const uint32_t m01 = sp[W], m23 = sp[W + 1];
+            const int ss = int(sp[W + 2]), slam = int(sp[W + 3]);
+            const int mm[4] = {int(m01 & 0xFFFFu), int(m01 >> 16), int(m23 & 0xFFFFu), int(m23 >> 16)};
+            __syncwarp();
+            w.apply_flips(p_mask, mm, ss, slam);
+            need_restore = true;
+            beta_dirty = true;
+        }
+
+        if (p_sched == a.nops) {  // a complete path
+            bool pass = true;
+            if (a.crc) {
+                ops += uint32_t(a.crc) * uint32_t(W);
+                uint32_t syn = 0u;
+                for (int r = 0; r < a.crc; ++r) {
+                    uint32_t par = 0u;
+                    for (int k = lane; k < W; k += 32) par ^= __popc(w.beta[k] & __ldg(a.crc_rows + size_t(r) * W + k));
+                    syn |= (par & 1u) << r;
+                }
+                syn = __reduce_xor_sync(FULL, syn);
+                pass = (syn == 0u);
+            }
+            if (pass) {
+                status = POLAR_OK;
+                out_pm = __uint_as_float(p_pmb);
+                out_src = 1;
+                break;
+            }
+            ++crc_fails;
+            if (!have_first) {
+                have_first = true;
+                first_pm = __uint_as_float(p_pmb);
+                uint32_t *sp = w.scr + size_t(D) * SW;
+                for (int k = lane; k < W; k += 32) sp[k] = w.beta[k];
+                __syncwarp();
+            }
+            if (crc_fails >= a.L) {
+                status = POLAR_CRC_FAIL;
+                out_pm = first_pm;
+                out_src = 2;
+                break;
+            }
+            continue;
+        }
+
+        // ---- recompute the alpha spine after a switch (Alg. calp) ----
+        if (need_restore) {
+            const uint32_t tgt = __ldg(&a.ops[p_sched].z);
+            if (tgt != NO_TARGET) {
+                const int lam_d = int(tgt & 0xFFu);
+                const int s_d = int(tgt >> 8);
+                ops += 2u * uint32_t(N - (1 << lam_d));
+                for (int lam = n - 1; lam >= lam_d; --lam) {
+                    const int sl = (s_d >> lam) << lam;
+                    if ((s_d >> lam) & 1) w.op_g(lam, sl);
+                    else w.op_f(lam);
+                }
+            }
+        }
+
+        // ---- walk the schedule to the next branching node ----
+        float pm = __uint_as_float(p_pmb);
+        int t = p_sched;
+        for (; t < a.nops; ++t) {
+            const uint4 op = __ldg(reinterpret_cast<const uint4 *>(a.ops) + t);
+            const uint32_t code = op.x & 0xFFu;
+            const int lam = int((op.x >> 8) & 0xFFu);
+            const int s = int(op.y);
+            if (code >= OP_BRANCH) break;
+            if (code == OP_F) {
+                w.op_f(lam);
+                ops += 2u << lam;
+            } else if (code == OP_G) {
+                w.op_g(lam, s);
+                ops += 2u << lam;
+            } else if (code == OP_COMB) {
+                w.op_comb(lam, s);
+                ops += (lam < 5) ? 1u : (1u << (lam - 5));
+            } else {  // Rate-0 node or frozen leaf: beta = 0, PM += sum HD(a)|a|
+                const float pen = w.halving_sum(w.stage(lam), lam, 1);
+                w.set_range(lam, s, 0u);
+                pm = __fadd_rn(pm, pen);
+                ops += (2u << lam) + 1u;
+            }
+        }
+        ++n_exp;
+        if (t == a.nops) {  // the path is complete: push it
+            const int slot = alloc_snapshot();
+            if (slot < 0) break;
+            write_snapshot(slot, N, 0u, 0u, 0, 0);
+            __syncwarp();
+            cur_snap = uint32_t(slot);
+            applied = 0u;
+            beta_dirty = false;
+            ops += 1u;
+            insert(__float_as_uint(pm), uint32_t(N) | (uint32_t(a.nops) << 16), seq_next++, uint32_t(slot));
+            continue;
+        }
+
+        // ---- branching node: visit counter and L-prune (Sec. 2.2.5) ----
+        const uint4 op = __ldg(reinterpret_cast<const uint4 *>(a.ops) + t);
+        const uint32_t code = op.x & 0xFFu;
+        const int lam = int((op.x >> 8) & 0xFFu);
+        const int s = int(op.y);
+        const int len = 1 << lam;
+        uint32_t c = 0;
+        if (lane == 0) c = ++w.cnt[op.w];
+        c = __shfl_sync(FULL, c, 0);
+        __syncwarp();
+        if (int(c) >= a.L) {
+            ops += a.stack_cost;
+            int removed = 0;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const bool kill = st.pm[j] != EMPTY && int(st.meta[j] & 0xFFFFu) <= s;
+                removed += __popc(__ballot_sync(FULL, kill));
+                if (kill) st.pm[j] = EMPTY;
+            }
+            count -= removed;
+        }
+
+        // ---- node candidates (Sec. 2.2.4 and readings R7-R9) ----
+        const float *A = w.stage(lam);
+        float delta[8];
+        uint32_t masks[8];
+        int nc = 0;
+        int m[4] = {0, 0, 0, 0};
+        if (code == OP_LEAF1) {
+            const float x = A[0];
+            w.write_hd(A, 0, s);
+            delta[0] = 0.0f;
+            masks[0] = 0u;
+            delta[1] = fabsf(x);
+            masks[1] = 1u;
+            nc = 2;
+            ops += 4u;
+        } else if (code == OP_REP) {
+            const float S = w.halving_sum(A, lam, 0);
+            const uint32_t bbit = S < 0.0f ? 1u : 0u;
+            const float p0 = w.halving_sum(A, lam, bbit ? 2 : 1);
+            w.set_range(lam, s, bbit);
+            delta[0] = p0;
+            masks[0] = 0u;
+            delta[1] = __fadd_rn(p0, fabsf(S));
+            masks[1] = FLIP_ALL;
+            nc = 2;
+            ops += 4u * uint32_t(len) + 3u;
+        } else if (code == OP_R1) {
+            float mag[4];
+            w.write_hd(A, lam, s);
+            w.least_k(A, lam, 2, m, mag);
+            delta[0] = 0.0f;
+            masks[0] = 0u;
+            delta[1] = mag[0];
+            masks[1] = 1u;
+            delta[2] = mag[1];
+            masks[2] = 2u;
+            delta[3] = __fadd_rn(mag[0], mag[1]);
+            masks[3] = 3u;
+            nc = 4;
+            ops += 6u * uint32_t(len) + 5u;
+        } else {  // OP_SPC
+            float mag[4];
+            const uint32_t q = w.write_hd(A, lam, s);
+            w.least_k(A, lam, 4, m, mag);
+            for (uint32_t mk = 0; mk < 16u; ++mk) {
+                const uint32_t pc = uint32_t(__popc(mk));
+                if ((pc & 1u) != q) continue;
+                float d = 0.0f;
+                for (int j = 0; j < 4; ++j)
+                    if ((mk >> j) & 1u) d = __fadd_rn(d, mag[j]);
+                delta[nc] = d;
+                masks[nc] = mk;
+                ++nc;
+                ops += 1u + (pc > 1u ? pc - 1u : 0u);
+            }
+            ops += 10u * uint32_t(len);
+        }
+
+        const int slot = alloc_snapshot();
+        if (slot < 0) break;
+        write_snapshot(slot, s + len, uint32_t(m[0]) | (uint32_t(m[1]) << 16), uint32_t(m[2]) | (uint32_t(m[3]) << 16),
+                       s, lam);
+        __syncwarp();
+        cur_snap = uint32_t(slot);
+        applied = 0u;
+        beta_dirty = false;
+        cm[0] = m[0];
+        cm[1] = m[1];
+        cm[2] = m[2];
+        cm[3] = m[3];
+        cs = s;
+        clam = lam;
+        const uint32_t base = seq_next;
+        seq_next += uint32_t(nc);
+        const uint32_t meta = uint32_t(s + len) | (uint32_t(t + 1) << 16);
+        for (int k = 0; k < nc; ++k)
+            insert(__float_as_uint(__fadd_rn(pm, delta[k])), meta, base + uint32_t(nc - 1 - k),
+                   uint32_t(slot) | (masks[k] << 8));
+    }
+
+    // ---- output: re-encode the codeword estimate, read the message ----
+    if (out_src == 2) {
+        const uint32_t *sp = w.scr + size_t(D) * SW;
+        for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
+    } else if (out_src == 0) {
+        for (int k = lane; k < W; k += 32) w.beta[k] = 0u;
+    }
+    __syncwarp();
+    ops += uint32_t(n) * uint32_t(W);
+    uint32_t *u = w.beta;
+    for (int k = lane; k < W; k += 32) {
+        uint32_t x = u[k];
+        if (N > 1) x ^= (x >> 1) & 0x55555555u;
+        if (N > 2) x ^= (x >> 2) & 0x33333333u;
+        if (N > 4) x ^= (x >> 4) & 0x0F0F0F0Fu;
+        if (N > 8) x ^= (x >> 8) & 0x00FF00FFu;
+        if (N > 16) x ^= (x >> 16) & 0x0000FFFFu;
+        u[k] = x;
+    }
+    __syncwarp();
+    for (int hw = 1; hw < W; hw <<= 1) {
+        for (int k = lane; k < W; k += 32)
+            if (!(k & hw)) u[k] ^= u[k + hw];
+        __syncwarp();
+    }
+    uint32_t *orow = a.info_out + size_t(b) * a.info_words;
+    for (int ow = lane; ow < a.info_words; ow += 32) {
+        uint32_t word = 0u;
+        for (int bb = 0; bb < 32; ++bb) {
+            const int j = ow * 32 + bb;
+            if (j < a.Kmsg) {
+                const int p = __ldg(a.msg_pos + j);
+                word |= ((u[p >> 5] >> (p & 31)) & 1u) << bb;
+            }
+        }
+        orow[ow] = word;
+    }
+    if (lane == 0) {
+        if (status == POLAR_TIMEOUT) out_pm = __int_as_float(0x7f800000);
+        a.pm_out[b] = out_pm;
+        a.status_out[b] = int8_t(status);
+        if (a.stats_out) {
+            uint32_t *sr = a.stats_out + size_t(b) * 4;
+            sr[0] = n_iter;
+            sr[1] = n_switch;
+            sr[2] = ops;
+            sr[3] = n_exp;
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(128) scs_decode_kernel(Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char *my = smem + size_t(wib) * a.warp_smem;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
+    Warp w{a, lane, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * a.N),
+           my + 4 * a.N + 4 * a.W, a.scratch + size_t(gwarp) * size_t(a.D + 1) * size_t(a.snap_words), nullptr};
+    for (;;) {
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(a.counter, 1u);
+        b = __shfl_sync(FULL, b, 0);
+        if (b >= unsigned(a.B)) break;
+        w.root = a.llr + size_t(b) * a.N;
+        decode_frame(a, w, b);
+    }
+}
+
+}  // namespace
+
+int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *d_llr, int B, int D, int L,
+                      uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream) {
+    if (B == 0) return 0;
+    Args a{};
+    a.llr = d_llr;
+    a.B = B;
+    a.N = p->N;
+    a.n = p->n;
+    a.W = p->W;
+    a.Kmsg = p->Kmsg;
+    a.crc = p->crc;
+    a.D = D;
+    a.L = L;
+    a.ops = dt->ops;
+    a.nops = int(p->ops.size());
+    a.nbranch = p->nbranch;
+    a.crc_rows = dt->crc_rows;
+    a.msg_pos = dt->msg_pos;
+    a.info_out = d_info;
+    a.info_words = (p->Kmsg + 31) / 32;
+    a.pm_out = d_pm;
+    a.status_out = d_status;
+    a.stats_out = d_stats;
+    a.snap_words = ((p->W + 4) + 7) & ~7;
+    a.max_iter = L * (p->nbranch + 9) + 2;
+    int lg = 0;
+    while ((1 << lg) < D) ++lg;
+    a.stack_cost = 2u * uint32_t(lg < 1 ? 1 : lg);
+    a.warp_smem = ((4 * p->N + 4 * p->W + p->nbranch) + 15) & ~15;
+
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int wpb = 4;
+    while (wpb > 1 && wpb * a.warp_smem > max_smem) wpb >>= 1;
+    if (wpb * a.warp_smem > max_smem) return POLAR_ELIMIT;
+    const int smem = wpb * a.warp_smem;
+    e = cudaFuncSetAttribute(scs_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel, wpb * 32, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) return POLAR_ELIMIT;
+    long long want = (long long)(B + wpb - 1) / wpb;
+    long long grid = (long long)sms * per_sm;
+    if (want < grid) grid = want;
+
+    const size_t warps = size_t(grid) * size_t(wpb);
+    const size_t scratch_words = warps * size_t(D + 1) * size_t(a.snap_words);
+    const size_t bytes = 64 + scratch_words * 4;
+    void *ws = nullptr;
+    e = cudaMallocAsync(&ws, bytes, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    a.counter = reinterpret_cast<unsigned *>(ws);
+    a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
+    e = cudaMemsetAsync(ws, 0, 64, stream);
+    if (e == cudaSuccess) {
+        scs_decode_kernel<<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(ws, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (e2 != cudaSuccess) return cuda_status(e2);
+    return 0;
+}
+
+}  // namespace polarscs
