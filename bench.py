@@ -1,0 +1,506 @@
+#!/usr/bin/env python3
+"""Throughput of batched FSSCS-RM decoding of polar codes on GB300.
+
+Workload (one step): PC(1024, 512) with CRC-16 (0x1021), Bhattacharyya
+frozen set at 0 dB design SNR, stack depth D = 32, visit cap L = 32, fast
+Rate-0/Rate-1/REP/SPC nodes, 1,048,576 BPSK/AWGN frames at each of
+Eb/N0 = 1.5, 2.0, 2.5 and 3.0 dB: four decode launches of 1,048,576 frames.
+Inputs are synthetic (seeded), encoded on the GPU and resident in HBM when
+the timed region starts; each launch reads 4 GiB of LLRs, far more than the
+129 MB L2, so no flush is needed between launches.
+
+Prints ONE JSON line (rank 0).  Metric: decoded message bits per second
+(496 per frame; the CRC bits are not counted).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one process per GPU): every rank decodes its own
+frames (seed offset by rank) with no collective on the data path (weak
+scaling); the timed region is bracketed by barriers and the slowest rank's
+time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(N=1024, K=512, crc=16, D=32, L=32, fast=True, frames=1 << 20, ebn0=(1.5, 2.0, 2.5, 3.0), seed=2,
+                design_snr_db=0.0)
+ALU_LANES_PER_SM = 128  # FP32/INT32 lanes per SM (4 partitions x 32)
+
+
+def workload_name(w=WORKLOAD) -> str:
+    return (f"PC({w['N']},{w['K']}) CRC-{w['crc']} FSSCS-RM D={w['D']} L={w['L']} fast nodes, "
+            f"{w['frames']} frames x Eb/N0 {'/'.join(str(e) for e in w['ebn0'])} dB")
+
+
+def bytes_per_frame(w=WORKLOAD) -> int:
+    """Algorithmic DRAM bytes of one frame: LLRs in, packed message + pm + status out."""
+    kmsg = w["K"] - w["crc"]
+    return 4 * w["N"] + 4 * ((kmsg + 31) // 32) + 4 + 1
+
+
+def rank_seed(rank: int, w=WORKLOAD) -> int:
+    return int(w["seed"]) + 1000 * int(rank)
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), source="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+def profiled_traffic(kernel_src: str, ebn0s) -> list[float] | None:
+    """DRAM bytes per frame at each Eb/N0 point from the committed ncu summary,
+    if it was taken on the current kernel source (its sha256 is recorded in
+    the summary) and covers every point; else None."""
+    path = os.path.join(ROOT, "profiles", "scs_decode_pc1024_traffic.txt")
+    try:
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        if kv.get("kernel_sha256") != sha:
+            return None
+        return [float(kv[f"dram_bytes_per_frame_{e}"]) for e in ebn0s]
+    except Exception:
+        return None
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Largest value over ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int) -> float:
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=reasons, samples=len(rows), power_w_max=max(power) if power else None)
+
+
+# --------------------------------------------------------------- inputs
+def make_gpu_inputs(ps, plan, frames: int, rank: int, w=WORKLOAD):
+    """Messages and noise from the seeded generators (host), encoded by the
+    GPU encoder, BPSK/AWGN LLRs formed on the GPU in float32 with the same
+    three rounded steps as workloads.bpsk_awgn_llr."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+
+    seed = rank_seed(rank, w)
+    kmsg = w["K"] - w["crc"]
+    msg = W.message_bits(seed, frames, kmsg)
+    d_msg = torch.from_numpy(ps.pack_bits(msg)).cuda()
+    del msg
+    d_cw = torch.empty((frames, plan.words), dtype=torch.int32, device="cuda")
+    ps.polar_encode_batch(plan, d_msg, d_cw)
+    shifts = torch.arange(32, dtype=torch.int32, device="cuda")
+    x = torch.empty((frames, w["N"]), dtype=torch.float32, device="cuda")
+    step = 1 << 16
+    for lo in range(0, frames, step):
+        bits = (d_cw[lo:lo + step].unsqueeze(-1) >> shifts) & 1
+        x[lo:lo + step] = 1.0 - 2.0 * bits.reshape(-1, w["N"]).to(torch.float32)
+    del d_cw
+    z = torch.from_numpy(W.awgn_noise(seed, frames, w["N"])).cuda()
+    llrs = []
+    for e in w["ebn0"]:
+        s, k = W.channel_constants(W.sigma_from_ebn0(e, w["K"] / w["N"]))
+        y = torch.mul(z, float(s))
+        y = torch.add(x, y)
+        llrs.append(torch.mul(y, float(k)))
+        del y
+    del z, x
+    torch.cuda.synchronize()
+    return llrs, d_msg
+
+
+def oracle_sample_inputs(frames: int, rank: int, w=WORKLOAD):
+    """The first `frames` frames of each point's batch, built on the host with
+    the oracle's encoder (CPU baseline / reference arm only)."""
+    import oracle
+    import workloads as W
+
+    seed = rank_seed(rank, w)
+    fr = oracle.construct(w["N"], w["K"], w["design_snr_db"])
+    kmsg = w["K"] - w["crc"]
+    msg = W.message_bits(seed, frames, kmsg)
+    cw = oracle.encode_batch(msg, w["N"], w["K"], fr, w["crc"])
+    z = W.awgn_noise(seed, frames, w["N"])
+    llrs = [W.bpsk_awgn_llr(cw, z, W.sigma_from_ebn0(e, w["K"] / w["N"])) for e in w["ebn0"]]
+    return fr, msg, llrs
+
+
+def run_oracle(fr, llrs, threads: int, w=WORKLOAD):
+    import oracle
+
+    t0 = time.perf_counter()
+    outs = [oracle.scs_decode_batch(l, w["N"], w["K"], fr, fast=w["fast"], D=w["D"], L=w["L"], crc_len=w["crc"],
+                                    threads=threads) for l in llrs]
+    return time.perf_counter() - t0, outs
+
+
+# ------------------------------------------------------------ reference arm
+def bench_reference(args, rank: int, world: int) -> None:
+    """The CPU oracle as it stands, timed on the host cores: each step decodes a
+    bounded sample (the first frames of every point) of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    sample = args.ref_frames
+    threads = os.cpu_count() or 1
+    fr, msg, llrs = oracle_sample_inputs(sample, 0)
+    for _ in range(args.warmup):
+        run_oracle(fr, llrs, threads)
+    times = []
+    for _ in range(args.steps):
+        dt, outs = run_oracle(fr, llrs, threads)
+        times.append(dt)
+    kmsg = WORKLOAD["K"] - WORKLOAD["crc"]
+    total = sum(times)
+    bits = kmsg * sample * len(WORKLOAD["ebn0"]) * args.steps
+    value = bits / total / 1e9
+    fer = {str(e): float(np.mean(np.any(o[0] != msg, axis=1))) for e, o in zip(WORKLOAD["ebn0"], outs)}
+    desc = f"oracle on {sample} frames per Eb/N0 point ({sample * len(WORKLOAD['ebn0'])} frames per step), {threads} host threads"
+    line = {"impl": "reference", "metric": "decoded info Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(), "sample": desc, "fer_sample": fer},
+            "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
+    import numpy as np
+    import torch
+
+    import paper_1809_03606_gb300 as ps
+
+    torch.cuda.set_device(local_rank)
+    ps.load(build_if_missing=True)
+    w = dict(WORKLOAD)
+    if args.frames:
+        w["frames"] = int(args.frames)
+    B, N, K, crc, D, L = w["frames"], w["N"], w["K"], w["crc"], w["D"], w["L"]
+    kmsg = K - crc
+    npts = len(w["ebn0"])
+    fr = ps.polar_construct(N, K, w["design_snr_db"])
+    plan = ps.Plan(N, K, fr, fast_nodes=w["fast"], crc=crc)
+    llrs, d_msg = make_gpu_inputs(ps, plan, B, rank, w)
+    outs = [(torch.empty((B, plan.msg_words), dtype=torch.int32, device="cuda"),
+             torch.empty(B, dtype=torch.float32, device="cuda"), torch.empty(B, dtype=torch.int8, device="cuda"))
+            for _ in range(npts)]
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for p in range(npts):
+            if events is not None:
+                events[p][0].record(stream)
+            ps.scs_decode_batch(plan, llrs[p], D, L, *outs[p], stream=stream)
+            if events is not None:
+                events[p][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # per-frame counters from one untimed launch per point (decoding is deterministic)
+    ops_pt, iters_pt, sw_pt, fer_pt, fail_pt = [], [], [], [], []
+    stats = torch.empty((B, 4), dtype=torch.int32, device="cuda")
+    for p in range(npts):
+        info, pm, st = outs[p]
+        ps.scs_decode_batch(plan, llrs[p], D, L, info, pm, st, stats, stream=stream)
+        torch.cuda.synchronize()
+        s64 = stats.to(torch.int64) & 0xFFFFFFFF
+        ops_pt.append(int(s64[:, 2].sum().item()))
+        iters_pt.append(float(s64[:, 0].double().mean().item()))
+        sw_pt.append(float(s64[:, 1].double().mean().item()))
+        fer_pt.append(float((info != d_msg).any(dim=1).double().mean().item()))
+        fail_pt.append(float((st != 0).double().mean().item()))
+    del stats
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    launch_events = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(npts)]
+                     for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.__enter__()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(launch_events[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    if sampler:
+        sampler.__exit__(None, None, None)
+    elapsed_ms = t_start.elapsed_time(t_end)
+    launch_ms = [[launch_events[k][p][0].elapsed_time(launch_events[k][p][1]) for p in range(npts)]
+                 for k in range(args.steps)]
+    elapsed_ms = reduce_max(elapsed_ms, world)
+    ms_per_step = elapsed_ms / args.steps
+    frames_all = reduce_sum(float(B * npts * args.steps), world)
+    value = frames_all * kmsg / (elapsed_ms / 1e3) / 1e9
+
+    # roofline of the decode kernel over the step: the slower of counted ALU
+    # operations at the FP32/INT32 lane peak and algorithmic bytes at HBM BW
+    peaks = measured_peaks()
+    info_dev = ps.polar_device_info()
+    sms = info_dev["sm_count"]
+    alu_peak = sms * ALU_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6  # lane-ops/s
+    hbm_peak = peaks["hbm_gbs"] * 1e9
+    kernel_s = sum(sum(r) for r in launch_ms) / args.steps / 1e3  # per step
+    bytes_step = B * npts * bytes_per_frame(w)
+    ops_step = float(sum(ops_pt))
+    t_alu, t_hbm = ops_step / alu_peak, bytes_step / hbm_peak
+    traffic_pf = profiled_traffic(os.path.join(ROOT, "paper_1809_03606_gb300", "csrc", "scs_decode.cu"), w["ebn0"])
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": ops_step / kernel_s / 1e12, "peak": alu_peak / 1e12, "unit": "Top/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_step / kernel_s / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None if traffic_pf is None else float(sum(traffic_pf)) * B  # bytes per step (all launches)
+    roof["peak_source"] = (f"{peaks['source']}: {sms} SMs x {ALU_LANES_PER_SM} lanes x {peaks['sm_max_mhz']:.0f} MHz"
+                           if roof["bound"] == "alu" else f"{peaks['source']} HBM copy bandwidth")
+    per_point = []
+    for p, e in enumerate(w["ebn0"]):
+        ms = statistics.mean(launch_ms[k][p] for k in range(args.steps))
+        ta, th = ops_pt[p] / alu_peak, B * bytes_per_frame(w) / hbm_peak
+        per_point.append({"ebn0_db": e, "ms": ms, "info_gbps": B * kmsg / (ms / 1e3) / 1e9, "fer": fer_pt[p],
+                          "crc_fail_rate": fail_pt[p], "pops_per_frame": iters_pt[p], "switches_per_frame": sw_pt[p],
+                          "ops_per_frame": ops_pt[p] / B, "bound": "alu" if ta >= th else "hbm",
+                          "roofline_frac": max(ta, th) / (ms / 1e3)})
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = bench_e2e(ps, plan, llrs, w, args, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_frames)
+    clocks = sampler.summary() if sampler else None
+
+    if rank == 0:
+        line = {"metric": "decoded info Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name(w), "frames_per_step_per_gpu": B * npts,
+                           "message_bits_per_frame": kmsg, "l2": "inputs larger than L2 (4 GiB of LLRs per launch)",
+                           "parallelism": f"frames sharded over {world} GPU(s), no data-path collective",
+                           "per_point": per_point},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": npts * args.steps,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
+def bench_e2e(ps, plan, llrs, w, args, world: int):
+    """Same metric through the C ABI with host buffers: every step copies its
+    LLRs from pinned host memory and reads the results back, in chunks whose
+    copies overlap the decode of the previous chunk."""
+    import torch
+
+    B, N = w["frames"], w["N"]
+    npts = len(llrs)
+    chunk = min(B, 1 << 17)
+    host = []
+    for l in llrs:
+        h = torch.empty((B, N), dtype=torch.float32, pin_memory=True)
+        h.copy_(l)
+        host.append(h)
+    out_host = [(torch.empty((B, plan.msg_words), dtype=torch.int32, pin_memory=True),
+                 torch.empty(B, dtype=torch.float32, pin_memory=True), torch.empty(B, dtype=torch.int8, pin_memory=True))
+                for _ in range(npts)]
+    dbuf = [torch.empty((chunk, N), dtype=torch.float32, device="cuda") for _ in range(2)]
+    dout = [(torch.empty((chunk, plan.msg_words), dtype=torch.int32, device="cuda"),
+             torch.empty(chunk, dtype=torch.float32, device="cuda"), torch.empty(chunk, dtype=torch.int8, device="cuda"))
+            for _ in range(2)]
+    copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    for e in free:
+        e.record(comp_s)
+
+    def one_step():
+        i = 0
+        for p in range(npts):
+            for lo in range(0, B, chunk):
+                hi = min(B, lo + chunk)
+                j = i & 1
+                with torch.cuda.stream(copy_s):
+                    copy_s.wait_event(free[j])
+                    dbuf[j][: hi - lo].copy_(host[p][lo:hi], non_blocking=True)
+                    ready[j].record(copy_s)
+                with torch.cuda.stream(comp_s):
+                    comp_s.wait_event(ready[j])
+                    o = [t[: hi - lo] for t in dout[j]]
+                    ps.scs_decode_batch(plan, dbuf[j][: hi - lo], w["D"], w["L"], *o, stream=comp_s)
+                    for src, dst in zip(o, out_host[p]):
+                        dst[lo:hi].copy_(src, non_blocking=True)
+                    free[j].record(comp_s)
+                i += 1
+
+    steps = max(1, min(args.steps, 3))
+    one_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_step()
+    torch.cuda.synchronize()
+    dt = reduce_max(time.perf_counter() - t0, world)
+    barrier(world)
+    kmsg = w["K"] - w["crc"]
+    frames = reduce_sum(float(B * npts * steps), world)
+    h2d = B * N * 4 * npts
+    d2h = B * (4 * plan.msg_words + 4 + 1) * npts
+    del host, out_host, dbuf, dout
+    return {"value": frames * kmsg / dt / 1e9, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps, "chunk_frames": chunk}
+
+
+def cpu_baseline(frames: int):
+    import os as _os
+
+    threads = _os.cpu_count() or 1
+    fr, msg, llrs = oracle_sample_inputs(frames, 0)
+    dt, _ = run_oracle(fr, llrs, threads)
+    kmsg = WORKLOAD["K"] - WORKLOAD["crc"]
+    nf = frames * len(llrs)
+    return {"value": nf * kmsg / dt / 1e9, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {frames} frames of each of the {len(llrs)} Eb/N0 points ({nf} frames), "
+                      f"decode-only wall time {dt:.2f} s on {threads} host threads"}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=0, help="frames per Eb/N0 point (default 1048576)")
+    ap.add_argument("--cpu-frames", type=int, default=8192, help="oracle sample per point for cpu_baseline")
+    ap.add_argument("--ref-frames", type=int, default=1024, help="oracle sample per point per step (reference arm)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        if args.impl == "ours":
+            import torch
+
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    try:
+        if args.impl == "reference":
+            bench_reference(args, rank, world)
+        else:
+            bench_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

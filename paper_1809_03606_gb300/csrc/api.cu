@@ -4,6 +4,7 @@
 // the host except argument validation and table building.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -16,6 +17,21 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
                       uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream);
 int launch_polar_encode(const polar_plan *p, const DeviceTables *dt, const uint32_t *d_msg, int B, uint32_t *d_cw,
                         cudaStream_t stream);
+
+// Per-call scratch comes from the device's default stream-ordered pool.  By
+// default that pool returns memory to the driver at every synchronisation,
+// which would turn each call's scratch into a fresh allocation; keep it.
+void keep_pool_memory(int dev) {
+    static std::atomic<unsigned long long> done{0ull};
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done.fetch_or(bit);
+}
 
 int cuda_status(int err) {
     const cudaError_t e = cudaError_t(err);

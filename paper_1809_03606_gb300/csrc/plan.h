@@ -69,5 +69,6 @@ uint32_t crc_polynomial(int crc);
 // Upload the plan's tables to the current device (once).  Returns 0 or an error.
 int plan_device(const polar_plan *plan, const DeviceTables **out);
 int cuda_status(int err);  // map a cudaError_t to POLAR_ECUDA / POLAR_ENOMEM
+void keep_pool_memory(int dev);
 
 }  // namespace polarscs

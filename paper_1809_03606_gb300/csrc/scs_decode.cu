@@ -765,6 +765,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     const size_t scratch_words = warps * size_t(D + 1) * size_t(a.snap_words);
     const size_t bytes = 64 + scratch_words * 4;
     void *ws = nullptr;
+    keep_pool_memory(dev);
     e = cudaMallocAsync(&ws, bytes, stream);
     if (e != cudaSuccess) return cuda_status(e);
     a.counter = reinterpret_cast<unsigned *>(ws);
