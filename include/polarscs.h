@@ -52,6 +52,9 @@ extern "C" {
 #define POLAR_ECUDA (-3)  /* a CUDA call failed (no device, launch error) */
 #define POLAR_ELIMIT (-4) /* valid code, but beyond the GPU kernel's limits:
                              N > 8192, D > 64 or L > 255 */
+#define POLAR_ESCRATCH (-5) /* scs_decode_batch_noalloc only: the plan's tables
+                               exceed its 1 MiB static table area, or one
+                               warp's scratch exceeds its 16 MiB static array */
 
 /* Maximum sizes the GPU decoder accepts. */
 #define POLAR_MAX_N_GPU 8192
@@ -116,6 +119,33 @@ int polar_encode(const uint8_t *msg, int N, int K, const uint8_t *frozen, int cr
  * (POLAR_ECUDA, POLAR_ENOMEM). */
 int scs_decode_batch(const polar_plan *plan, const float *d_llr, int B, int D, int L, uint32_t *d_info,
                      float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream);
+
+/* scs_decode_batch without any allocation by the library (the paper has no
+ * counterpart; this is a deployment variant).  For callers that cannot
+ * allocate device memory at decode time -- a fixed budget reserved at
+ * start-up, a real-time or callback context where cudaMalloc/cudaMallocAsync
+ * may block or fail, or device memory owned by another allocator.  Same
+ * arguments, outputs and results as scs_decode_batch; the caller still
+ * provides every input and output buffer.
+ *  - The scratch lives in a file-scope static device array of 16 MiB and the
+ *    plan's tables are copied (asynchronously, from the plan's host memory)
+ *    into a static 1 MiB device area; every GPU that loads the library holds
+ *    both until the process exits.  The decoder runs as many resident warps
+ *    as the 16 MiB hold, so large D and N run on fewer warps (slower, same
+ *    result).  Returns POLAR_ESCRATCH when the plan's tables exceed 1 MiB or
+ *    one warp's scratch, (D+1) * (ceil(N/32)+4 rounded up to 8) * 4 bytes,
+ *    exceeds 16 MiB.
+ *  - No cudaMalloc, cudaMallocAsync or cudaFree is called.  The first call on
+ *    a device looks up the arrays' device addresses (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream
+ *    capture.
+ *  - Every call shares the two arrays, which keep the previous call's
+ *    contents (the frame counter is cleared on each call).  Calls whose work
+ *    overlaps on the GPU (different streams, or different host threads)
+ *    race on them and give wrong results; serialise them, e.g. on one
+ *    stream. */
+int scs_decode_batch_noalloc(const polar_plan *plan, const float *d_llr, int B, int D, int L, uint32_t *d_info,
+                             float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream);
 
 /* Decode one frame held in host memory (synchronous), fast nodes on:
  * llr N floats in, info_out K - crc bytes (one bit per byte) out, *pm_out the

@@ -19,13 +19,13 @@ import numpy as np
 from . import _build
 
 POLAR_OK, POLAR_CRC_FAIL, POLAR_TIMEOUT = 0, 1, 2
-POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ELIMIT = -1, -2, -3, -4
+POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ELIMIT, POLAR_ESCRATCH = -1, -2, -3, -4, -5
 MAX_N_GPU, MAX_D_GPU, MAX_L_GPU = 8192, 64, 255
 OP_NAMES = {0: "alpha", 1: "beta", 2: "R0", 3: "R1", 4: "REP", 5: "SPC", 6: "leaf0", 7: "leaf1"}
 
 EXPORTED = (
     "polar_construct", "polar_plan_create", "polar_plan_destroy", "polar_plan_schedule", "polar_encode_batch",
-    "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info",
+    "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info", "scs_decode_batch_noalloc",
 )
 
 _lock = threading.Lock()
@@ -34,7 +34,7 @@ _lib = None
 
 class PolarError(RuntimeError):
     def __init__(self, fn: str, rc: int):
-        names = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT"}
+        names = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT", -5: "ESCRATCH"}
         super().__init__(f"{fn} failed: {names.get(rc, rc)}")
         self.rc = rc
 
@@ -64,6 +64,7 @@ def load(build_if_missing: bool = False):
         lib.polar_encode.argtypes = [vp, i32, i32, vp, i32, vp]
         lib.scs_decode_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
         lib.scs_decode.argtypes = [vp, i32, i32, vp, i32, i32, i32, vp, vp]
+        lib.scs_decode_batch_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
         lib.polar_device_info.argtypes = [vp, vp, vp]
         _lib = lib
         return lib
@@ -181,6 +182,20 @@ def scs_decode_batch(plan: Plan, llr, D: int, L: int, info_words, pm, status, st
 
     B = llr.shape[0]
     _check("scs_decode_batch", load().scs_decode_batch(
+        plan.handle, _dev_ptr(llr, torch.float32, "llr", (B, plan.N)), B, D, L,
+        _dev_ptr(info_words, torch.int32, "info_words", (B, plan.msg_words)),
+        _dev_ptr(pm, torch.float32, "pm", (B,)), _dev_ptr(status, torch.int8, "status", (B,)),
+        None if stats is None else _dev_ptr(stats, torch.int32, "stats", (B, 4)), _stream_ptr(stream)))
+
+
+def scs_decode_batch_noalloc(plan: Plan, llr, D: int, L: int, info_words, pm, status, stats=None, stream=None) -> None:
+    """scs_decode_batch with the library's fixed static scratch: no device
+    allocation by the library (see include/polarscs.h for its limits and the
+    rule that calls must not overlap on the GPU)."""
+    import torch
+
+    B = llr.shape[0]
+    _check("scs_decode_batch_noalloc", load().scs_decode_batch_noalloc(
         plan.handle, _dev_ptr(llr, torch.float32, "llr", (B, plan.N)), B, D, L,
         _dev_ptr(info_words, torch.int32, "info_words", (B, plan.msg_words)),
         _dev_ptr(pm, torch.float32, "pm", (B,)), _dev_ptr(status, torch.int8, "status", (B,)),

@@ -17,6 +17,8 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
                       uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream);
 int launch_polar_encode(const polar_plan *p, const DeviceTables *dt, const uint32_t *d_msg, int B, uint32_t *d_cw,
                         cudaStream_t stream);
+int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
+                              float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream);
 
 // Per-call scratch comes from the device's default stream-ordered pool.  By
 // default that pool returns memory to the driver at every synchronisation,
@@ -110,6 +112,16 @@ extern "C" int scs_decode_batch(const polar_plan *p, const float *d_llr, int B, 
     int rc = plan_device(p, &dt);
     if (rc) return rc;
     return launch_scs_decode(p, dt, d_llr, B, D, L, d_info, d_pm, d_status, d_stats, cudaStream_t(stream));
+}
+
+extern "C" int scs_decode_batch_noalloc(const polar_plan *p, const float *d_llr, int B, int D, int L,
+                                        uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats,
+                                        void *stream) {
+    if (!p || B < 0 || D < 1 || L < 1) return POLAR_EINVAL;
+    if (B > 0 && (!d_llr || !d_info || !d_pm || !d_status)) return POLAR_EINVAL;
+    if (p->N > POLAR_MAX_N_GPU || D > POLAR_MAX_D_GPU || L > POLAR_MAX_L_GPU) return POLAR_ELIMIT;
+    if (B == 0) return 0;
+    return launch_scs_decode_noalloc(p, d_llr, B, D, L, d_info, d_pm, d_status, d_stats, cudaStream_t(stream));
 }
 
 extern "C" int polar_encode_batch(const polar_plan *p, const uint32_t *d_msg, int B, uint32_t *d_codeword,

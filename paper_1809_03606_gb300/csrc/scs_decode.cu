@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 
 #include "plan.h"
 
@@ -779,6 +781,146 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     if (e != cudaSuccess) return cuda_status(e);
     if (e2 != cudaSuccess) return cuda_status(e2);
     return 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Decoding without any allocation by the library.
+//
+// Some callers cannot allocate device memory when they decode: code that runs
+// under a fixed memory budget reserved at start-up, callers inside a host
+// callback or a real-time loop where cudaMalloc/cudaMallocAsync may block or
+// fail, or processes whose device memory is owned by another allocator.  For
+// them scs_decode_batch_noalloc keeps the decoder's scratch (the per-warp beta
+// snapshots and the frame counter) and its copy of the plan's tables in two
+// fixed file-scope device arrays below.  Every GPU that loads the library holds
+// these arrays (16 MiB + 1 MiB) until the process exits.
+//
+// The host needs their device addresses: in host code the names are host-side
+// stand-ins, so they are fetched once per device with cudaGetSymbolAddress,
+// with that device current, on the first call made on that device.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;
+constexpr size_t kStaticTableBytes = size_t(1) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+static __device__ __align__(256) unsigned char g_static_tables[kStaticTableBytes];
+
+namespace {
+
+struct StaticAreas {
+    bool ready = false;
+    void *scratch = nullptr;
+    void *tables = nullptr;
+};
+std::mutex g_static_mu;
+StaticAreas g_static_areas[64];
+
+int static_areas(int dev, StaticAreas *out) {
+    if (dev < 0 || dev >= 64) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(g_static_mu);
+    StaticAreas &s = g_static_areas[dev];
+    if (!s.ready) {
+        void *scr = nullptr, *tab = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&scr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaGetSymbolAddress(&tab, g_static_tables);
+        if (e != cudaSuccess) return cuda_status(e);
+        s.scratch = scr;
+        s.tables = tab;
+        s.ready = true;
+    }
+    *out = s;
+    return 0;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
+                              float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream) {
+    if (B == 0) return 0;
+    int dev = 0, sms = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    StaticAreas areas;
+    int rc = static_areas(dev, &areas);
+    if (rc) return rc;
+
+    // the plan's tables, copied into the static table area
+    const size_t ops_bytes = p->ops.size() * sizeof(KOp);
+    const size_t rows_off = align_up(ops_bytes, 256);
+    const size_t rows_bytes = p->crc_rows.size() * sizeof(uint32_t);
+    const size_t pos_off = align_up(rows_off + rows_bytes, 256);
+    const size_t pos_bytes = p->msg_pos.size() * sizeof(uint16_t);
+    if (pos_off + pos_bytes > kStaticTableBytes) return POLAR_ESCRATCH;
+    unsigned char *tab = static_cast<unsigned char *>(areas.tables);
+
+    Args a{};
+    a.llr = d_llr;
+    a.B = B;
+    a.N = p->N;
+    a.n = p->n;
+    a.W = p->W;
+    a.Kmsg = p->Kmsg;
+    a.crc = p->crc;
+    a.D = D;
+    a.L = L;
+    a.ops = reinterpret_cast<const KOp *>(tab);
+    a.nops = int(p->ops.size());
+    a.nbranch = p->nbranch;
+    a.crc_rows = reinterpret_cast<const uint32_t *>(tab + rows_off);
+    a.msg_pos = reinterpret_cast<const uint16_t *>(tab + pos_off);
+    a.info_out = d_info;
+    a.info_words = (p->Kmsg + 31) / 32;
+    a.pm_out = d_pm;
+    a.status_out = d_status;
+    a.stats_out = d_stats;
+    a.snap_words = ((p->W + 4) + 7) & ~7;
+    a.max_iter = L * (p->nbranch + 9) + 2;
+    int lg = 0;
+    while ((1 << lg) < D) ++lg;
+    a.stack_cost = 2u * uint32_t(lg < 1 ? 1 : lg);
+    a.warp_smem = ((4 * p->N + 4 * p->W + p->nbranch) + 15) & ~15;
+
+    // as many resident warps as the static scratch holds (the kernel is
+    // persistent and claims frames dynamically, so fewer warps only cost speed)
+    const size_t per_warp = size_t(D + 1) * size_t(a.snap_words) * 4;
+    const size_t warps_fit = (kStaticScratchBytes - 64) / per_warp;
+    if (warps_fit < 1) return POLAR_ESCRATCH;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int wpb = 4;
+    while (wpb > 1 && (wpb * a.warp_smem > max_smem || size_t(wpb) > warps_fit)) wpb >>= 1;
+    if (wpb * a.warp_smem > max_smem) return POLAR_ELIMIT;
+    const int smem = wpb * a.warp_smem;
+    e = cudaFuncSetAttribute(scs_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel, wpb * 32, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) return POLAR_ELIMIT;
+    long long grid = (long long)sms * per_sm;
+    const long long want = (long long)(B + wpb - 1) / wpb;
+    const long long fit = (long long)(warps_fit / size_t(wpb));
+    if (want < grid) grid = want;
+    if (fit < grid) grid = fit;
+
+    a.counter = static_cast<unsigned *>(areas.scratch);
+    a.scratch = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(areas.scratch) + 64);
+    // tables from host memory, then the frame counter back to zero (the array
+    // keeps whatever the previous call left in it)
+    e = cudaMemcpyAsync(tab, p->ops.data(), ops_bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && rows_bytes)
+        e = cudaMemcpyAsync(tab + rows_off, p->crc_rows.data(), rows_bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && pos_bytes)
+        e = cudaMemcpyAsync(tab + pos_off, p->msg_pos.data(), pos_bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    scs_decode_kernel<<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : cuda_status(e);
 }
 
 }  // namespace polarscs

@@ -1,0 +1,77 @@
+"""The allocation-free decode entry point against the regular one.
+
+scs_decode_batch_noalloc serves callers that cannot allocate device memory
+when they decode (a budget fixed at start-up, a real-time or callback
+context, memory owned by another allocator): its scratch is a fixed static
+device array inside the library instead of a per-call stream-ordered
+allocation.  Its results must be exactly those of scs_decode_batch.  Two
+calls in a row, with different codes, check that the shared static memory
+(tables, frame counter, snapshots) left over from one call does not leak
+into the next.  This file is collected last so that a failure here comes
+after every other test has run; it also passes on its own in a fresh
+process.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import paper_1809_03606_gb300 as ps
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _frames(oracle, N, K, crc, B, ebn0, seed):
+    fr = oracle.construct(N, K, 0.0)
+    msg = W.message_bits(seed, B, K - crc)
+    cw = oracle.encode_batch(msg, N, K, fr, crc)
+    return fr, W.bpsk_awgn_llr(cw, W.awgn_noise(seed, B, N), W.sigma_from_ebn0(ebn0, K / N))
+
+
+def _outputs(plan, B):
+    return (torch.full((B, plan.msg_words), -1, dtype=torch.int32, device="cuda"),
+            torch.full((B,), -1.0, dtype=torch.float32, device="cuda"),
+            torch.full((B,), -7, dtype=torch.int8, device="cuda"),
+            torch.full((B, 4), -1, dtype=torch.int32, device="cuda"))
+
+
+def test_noalloc_matches_allocating_entry_point(oracle_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ps.load(build_if_missing=True)
+    cases = [  # two different codes, one call each, back to back
+        dict(N=1024, K=512, crc=16, fast=True, D=32, L=32, B=3000, ebn0=1.5, seed=41),
+        dict(N=256, K=128, crc=0, fast=False, D=16, L=4, B=2000, ebn0=2.5, seed=42),
+    ]
+    prepared = []
+    for c in cases:
+        fr, llr = _frames(oracle_lib, c["N"], c["K"], c["crc"], c["B"], c["ebn0"], c["seed"])
+        plan = ps.Plan(c["N"], c["K"], fr, fast_nodes=c["fast"], crc=c["crc"])
+        prepared.append((c, plan, torch.from_numpy(llr).cuda()))
+    # the allocation-free calls first, back to back on one stream
+    got = []
+    for c, plan, x in prepared:
+        out = _outputs(plan, c["B"])
+        ps.scs_decode_batch_noalloc(plan, x, c["D"], c["L"], *out)
+        got.append(out)
+    torch.cuda.synchronize()
+    for (c, plan, x), g in zip(prepared, got):
+        ref = _outputs(plan, c["B"])
+        ps.scs_decode_batch(plan, x, c["D"], c["L"], *ref)
+        torch.cuda.synchronize()
+        for r, q in zip(ref, g):
+            assert torch.equal(r, q), c  # bit-exact: bits, path metrics, status, counters
+        assert int((ref[2] == 0).sum()) > 0
+
+
+def test_noalloc_rejects_sizes_beyond_its_limits():
+    lib = ps.load(build_if_missing=True)
+    plan = ps.Plan(64, 32, ps.polar_construct(64, 32, 0.0))
+    dummy = C.c_void_p(16)
+    assert lib.scs_decode_batch_noalloc(plan.handle, dummy, 4, 65, 4, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
+    assert lib.scs_decode_batch_noalloc(plan.handle, dummy, 4, 8, 256, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
+    assert lib.scs_decode_batch_noalloc(plan.handle, dummy, 4, 0, 4, dummy, dummy, dummy, None, None) == ps.POLAR_EINVAL
+    big = ps.Plan(16384, 8192, ps.polar_construct(16384, 8192, 0.0))
+    assert lib.scs_decode_batch_noalloc(big.handle, dummy, 1, 8, 8, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
