@@ -40,20 +40,22 @@ class PolarError(RuntimeError):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library this process loads: $POLARSCS_LIB if set, else the in-tree build."""
+    return os.environ.get("POLARSCS_LIB") or _build.LIB
 
 
 def load(build_if_missing: bool = False):
-    """Load libpolarscs.so (building it first only if asked)."""
+    """Load libpolarscs.so (building the in-tree library first only if asked)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if build_if_missing:
+        path = lib_path()
+        if build_if_missing and path == _build.LIB:
             _build.build()
-        if not os.path.exists(_build.LIB):
-            raise ImportError(f"libpolarscs.so is not built ({_build.LIB}); run __graft_entry__.build()")
-        lib = C.CDLL(_build.LIB)
+        if not os.path.exists(path):
+            raise ImportError(f"libpolarscs.so is not built ({path}); run __graft_entry__.build()")
+        lib = C.CDLL(path)
         vp, i32, f32 = C.c_void_p, C.c_int, C.c_float
         lib.polar_construct.argtypes = [i32, i32, f32, vp]
         lib.polar_plan_create.argtypes = [i32, i32, vp, i32, i32, C.POINTER(vp)]

@@ -46,15 +46,19 @@ def needs_build() -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and not needs_build():
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, variant: str = "") -> str:
+    """Build the library.  variant="timers" builds a separate debug library
+    (libpolarscs_timers.so) with the per-phase cycle counters compiled in."""
+    lib = LIB if not variant else os.path.join(BUILD, f"libpolarscs_{variant}.so")
+    defines = {"": [], "timers": ["-DPOLAR_PHASE_TIMERS"]}[variant]
+    if not force and not variant and not needs_build():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + (f".{variant}" if variant else "") + ".o")
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *defines, "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info and src.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -66,13 +70,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("nvcc link of libpolarscs.so failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

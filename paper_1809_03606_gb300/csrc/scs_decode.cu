@@ -37,6 +37,13 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;  // path-metric bits of an empty slot
 constexpr uint32_t NOSNAP = 0xFFu;       // snapshot id of the initial path
 constexpr uint32_t FLIP_ALL = 16u;       // REP second candidate: flip every bit
+// SPC candidates (reading R8): the 8 flip masks over the four least reliable
+// positions whose parity equals the hard-decision parity, ascending, packed
+// one 4-bit mask per nibble
+constexpr uint32_t SPC_MASKS_EVEN = 0xFCA96530u;  // 0,3,5,6,9,10,12,15
+constexpr uint32_t SPC_MASKS_ODD = 0xEDB87421u;   // 1,2,4,7,8,11,13,14
+constexpr uint32_t R1_MASKS = 0x3210u;            // Chase-II: none, m1, m2, both
+constexpr uint32_t LEAF1_MASKS = 0x10u;           // decision, flipped decision
 
 struct Args {
     const float *llr;
@@ -56,7 +63,23 @@ struct Args {
     int max_iter;
     uint32_t stack_cost;
     int warp_smem;  // bytes of shared memory per warp
+    int llr_vec;    // the LLR rows are 16-byte aligned: vector loads of the root
 };
+
+// Optional per-phase cycle counters (debug builds with -DPOLAR_PHASE_TIMERS):
+// lane 0 of every warp adds clock64() deltas per phase of the search into a
+// device array read back by polar_phase_cycles().  Off by default.
+enum Phase { PH_POP, PH_BETA, PH_ALPHA, PH_FG, PH_COMB, PH_R0, PH_NODE, PH_SNAP, PH_INSERT, PH_PRUNE, PH_DONE, PH_OUT, PH_N };
+#ifdef POLAR_PHASE_TIMERS
+__device__ unsigned long long g_phase_cycles[PH_N];
+#define PT_INIT long long pt_t = clock64(); unsigned long long pt_acc[PH_N] = {};
+#define PT(ph) { const long long pt_n = clock64(); pt_acc[ph] += (unsigned long long)(pt_n - pt_t); pt_t = pt_n; }
+#define PT_FLUSH if (lane == 0) { for (int q = 0; q < PH_N; ++q) atomicAdd(&g_phase_cycles[q], pt_acc[q]); }
+#else
+#define PT_INIT
+#define PT(ph)
+#define PT_FLUSH
+#endif
 
 __device__ __forceinline__ float f_minsum(float a, float b) {
     // Eq. minsum: sign(a) sign(b) min(|a|, |b|); the sign bit is the XOR of
@@ -66,10 +89,10 @@ __device__ __forceinline__ float f_minsum(float a, float b) {
     return __uint_as_float(__float_as_uint(m) | sg);
 }
 
+// Eq. minsum / Fig. minsum: g = b + (1 - 2 beta) a, a = alpha_p[i],
+// b = alpha_p[i + Lambda].  b + (-a) is b - a exactly in IEEE arithmetic.
 __device__ __forceinline__ float g_op(float a, float b, uint32_t bit) {
-    // Eq. minsum / Fig. minsum: g = b + (1 - 2 beta) a, a = alpha_p[i],
-    // b = alpha_p[i + Lambda]
-    return bit ? __fsub_rn(b, a) : __fadd_rn(b, a);
+    return __fadd_rn(b, __uint_as_float(__float_as_uint(a) ^ (bit << 31)));
 }
 
 __device__ __forceinline__ float pen_transform(float x, int mode) {
@@ -89,13 +112,36 @@ struct Warp {
     const float *root;
 
     __device__ const float *stage(int lam) const { return lam == a.n ? root : alpha + (1 << lam); }
+    __device__ bool vec_ok(int plam) const { return plam < a.n || a.llr_vec; }
 
-    // alpha of the even child (lamc, sc) from its parent (Eq. llrcalc, f)
+    // alpha of the even child (lamc) from its parent (Eq. llrcalc, f)
     __device__ void op_f(int lamc) const {
         const int len = 1 << lamc;
         const float *P = stage(lamc + 1);
         float *C = alpha + len;
-        for (int i = lane; i < len; i += 32) C[i] = f_minsum(P[i], P[i + len]);
+        if (len >= 128 && vec_ok(lamc + 1)) {
+            for (int i = 4 * lane; i < len; i += 128) {
+                const float4 x = *reinterpret_cast<const float4 *>(P + i);
+                const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
+                float4 r;
+                r.x = f_minsum(x.x, y.x);
+                r.y = f_minsum(x.y, y.y);
+                r.z = f_minsum(x.z, y.z);
+                r.w = f_minsum(x.w, y.w);
+                *reinterpret_cast<float4 *>(C + i) = r;
+            }
+        } else if (len >= 64 && vec_ok(lamc + 1)) {
+            for (int i = 2 * lane; i < len; i += 64) {
+                const float2 x = *reinterpret_cast<const float2 *>(P + i);
+                const float2 y = *reinterpret_cast<const float2 *>(P + i + len);
+                float2 r;
+                r.x = f_minsum(x.x, y.x);
+                r.y = f_minsum(x.y, y.y);
+                *reinterpret_cast<float2 *>(C + i) = r;
+            }
+        } else {
+            for (int i = lane; i < len; i += 32) C[i] = f_minsum(P[i], P[i + len]);
+        }
         __syncwarp();
     }
 
@@ -106,10 +152,36 @@ struct Warp {
         const int sl = sc - len;
         const float *P = stage(lamc + 1);
         float *C = alpha + len;
-        for (int i = lane; i < len; i += 32) {
-            const int pos = sl + i;
-            const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
-            C[i] = g_op(P[i], P[i + len], bit);
+        if (len >= 128 && vec_ok(lamc + 1)) {
+            for (int i = 4 * lane; i < len; i += 128) {
+                const int pos = sl + i;  // a multiple of 4: the 4 bits share a word
+                const uint32_t bits = beta[pos >> 5] >> (pos & 31);
+                const float4 x = *reinterpret_cast<const float4 *>(P + i);
+                const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
+                float4 r;
+                r.x = g_op(x.x, y.x, bits & 1u);
+                r.y = g_op(x.y, y.y, (bits >> 1) & 1u);
+                r.z = g_op(x.z, y.z, (bits >> 2) & 1u);
+                r.w = g_op(x.w, y.w, (bits >> 3) & 1u);
+                *reinterpret_cast<float4 *>(C + i) = r;
+            }
+        } else if (len >= 64 && vec_ok(lamc + 1)) {
+            for (int i = 2 * lane; i < len; i += 64) {
+                const int pos = sl + i;
+                const uint32_t bits = beta[pos >> 5] >> (pos & 31);
+                const float2 x = *reinterpret_cast<const float2 *>(P + i);
+                const float2 y = *reinterpret_cast<const float2 *>(P + i + len);
+                float2 r;
+                r.x = g_op(x.x, y.x, bits & 1u);
+                r.y = g_op(x.y, y.y, (bits >> 1) & 1u);
+                *reinterpret_cast<float2 *>(C + i) = r;
+            }
+        } else {
+            for (int i = lane; i < len; i += 32) {
+                const int pos = sl + i;
+                const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
+                C[i] = g_op(P[i], P[i + len], bit);
+            }
         }
         __syncwarp();
     }
@@ -144,10 +216,11 @@ struct Warp {
         __syncwarp();
     }
 
-    // hard decisions of the node's alpha into beta[s, s + 2^lam); returns
-    // their parity (XOR)
-    __device__ uint32_t write_hd(const float *A, int lam, int s) const {
+    // ---- reductions of the node decoders over the node's alpha ----
+    // hard decisions into beta[s, s + 2^lam); returns their parity (XOR)
+    __device__ uint32_t node_hd(int lam, int s) const {
         const int len = 1 << lam;
+        const float *A = stage(lam);
         uint32_t par = 0;
         if (len >= 32) {
             for (int c = 0; c < (len >> 5); ++c) {
@@ -170,8 +243,9 @@ struct Warp {
     // sum over the node's 2^lam alpha values (transformed) in halving order:
     // v[i] += v[i + h], h = 2^(lam-1) ... 1.  Levels wider than a warp are
     // written into the free alpha stages below the node.
-    __device__ float halving_sum(const float *A, int lam, int mode) const {
+    __device__ float node_sum(int lam, int mode) const {
         const int len = 1 << lam;
+        const float *A = stage(lam);
         if (len <= 32) {
             float v = lane < len ? pen_transform(A[lane], mode) : 0.0f;
             for (int h = len >> 1; h >= 1; h >>= 1) {
@@ -201,14 +275,53 @@ struct Warp {
         return __shfl_sync(FULL, v, 0);
     }
 
-    // the k least reliable positions (|alpha|, ties to the lower index)
-    __device__ void least_k(const float *A, int lam, int k, int *m, float *mag) const {
+    // REP node of at most 32 values: S = sum alpha, and the penalties of the
+    // all-zero and all-one words, each summed in halving order in one tree
+    __device__ void rep_sums(int lam, float &S, float &pen0, float &pen1) const {
         const int len = 1 << lam;
-        for (int j = 0; j < k; ++j) {
+        const float *A = stage(lam);
+        const float x = lane < len ? A[lane] : 0.0f;
+        float v = x, p0 = pen_transform(x, 1), p1 = lane < len ? pen_transform(x, 2) : 0.0f;
+        for (int h = len >> 1; h >= 1; h >>= 1) {
+            const float ov = __shfl_down_sync(FULL, v, h);
+            const float o0 = __shfl_down_sync(FULL, p0, h);
+            const float o1 = __shfl_down_sync(FULL, p1, h);
+            if (lane < h) {
+                v = __fadd_rn(v, ov);
+                p0 = __fadd_rn(p0, o0);
+                p1 = __fadd_rn(p1, o1);
+            }
+        }
+        S = __shfl_sync(FULL, v, 0);
+        pen0 = __shfl_sync(FULL, p0, 0);
+        pen1 = __shfl_sync(FULL, p1, 0);
+    }
+
+    // the k least reliable positions (|alpha|, ties to the lower index)
+    __device__ void node_least(int lam, int k, int *m, float *mag) const {
+        const int len = 1 << lam;
+        const float *A = stage(lam);
+        if (len <= 32) {  // one value per lane: k rounds of warp minima
+            uint32_t v = lane < len ? __float_as_uint(fabsf(A[lane])) : EMPTY;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= k) break;
+                const uint32_t gv = __reduce_min_sync(FULL, v);
+                const uint32_t gi = __reduce_min_sync(FULL, v == gv ? uint32_t(lane) : EMPTY);
+                m[j] = int(gi);
+                mag[j] = __uint_as_float(gv);
+                if (uint32_t(lane) == gi) v = EMPTY;
+            }
+            return;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= k) break;
             uint32_t bv = EMPTY, bi = EMPTY;
             for (int i = lane; i < len; i += 32) {
                 bool used = false;
-                for (int q = 0; q < j; ++q) used |= (m[q] == i);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) used |= (q < j) && (m[q] == i);
                 if (used) continue;
                 const uint32_t v = __float_as_uint(fabsf(A[i]));
                 if (v < bv) {
@@ -234,6 +347,7 @@ struct Warp {
             }
         }
         if (lane == 0) {
+#pragma unroll
             for (int j = 0; j < 4; ++j)
                 if ((mask >> j) & 1u) {
                     const int pos = s + m[j];
@@ -250,11 +364,178 @@ struct Stack {
 
 __device__ __forceinline__ bool slot_exists(int j, int lane, int D) { return j * 32 + lane < D; }
 
-__device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
+// Candidates of one expansion, described compactly so that every lane can
+// produce any candidate r from registers: flip mask r is nibble r of `masks`
+// (REP: candidate 1 flips all), and its path-metric delta is the ascending
+// sum of the flipped positions' |alpha| (REP: rep0 / rep1).
+struct Cands {
+    int nc;
+    uint32_t masks;
+    bool rep;
+    float rep0, rep1;
+    float mag[4];
+
+    __device__ __forceinline__ uint32_t mask(int r) const { return rep ? (r ? FLIP_ALL : 0u) : ((masks >> (4 * r)) & 0xFu); }
+    __device__ __forceinline__ float delta(int r) const {
+        if (rep) return r ? rep1 : rep0;
+        const uint32_t mk = (masks >> (4 * r)) & 0xFu;
+        float d = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((mk >> j) & 1u) d = __fadd_rn(d, mag[j]);
+        return d;
+    }
+};
+
+// CRC syndrome of the codeword estimate in beta: zero iff the message's CRC
+// matches (the long division is linear, so the syndrome is a fixed GF(2)
+// matrix applied to the codeword bits)
+__device__ __noinline__ bool crc_ok(const Args &a, const uint32_t *beta, int lane) {
+    uint32_t syn = 0u;
+    for (int r = 0; r < a.crc; ++r) {
+        uint32_t par = 0u;
+        for (int k = lane; k < a.W; k += 32) par ^= __popc(beta[k] & __ldg(a.crc_rows + size_t(r) * a.W + k));
+        syn |= (par & 1u) << r;
+    }
+    return __reduce_xor_sync(FULL, syn) == 0u;
+}
+
+// output: re-encode the codeword estimate (F is an involution, Sec. 2.2.2)
+// and read the message bits off the information set
+__device__ __noinline__ void write_output(const Args &a, uint32_t *u, unsigned b, int lane) {
+    const int W = a.W, N = a.N;
+    for (int k = lane; k < W; k += 32) {
+        uint32_t x = u[k];
+        if (N > 1) x ^= (x >> 1) & 0x55555555u;
+        if (N > 2) x ^= (x >> 2) & 0x33333333u;
+        if (N > 4) x ^= (x >> 4) & 0x0F0F0F0Fu;
+        if (N > 8) x ^= (x >> 8) & 0x00FF00FFu;
+        if (N > 16) x ^= (x >> 16) & 0x0000FFFFu;
+        u[k] = x;
+    }
+    __syncwarp();
+    for (int hw = 1; hw < W; hw <<= 1) {
+        for (int k = lane; k < W; k += 32)
+            if (!(k & hw)) u[k] ^= u[k + hw];
+        __syncwarp();
+    }
+    uint32_t *orow = a.info_out + size_t(b) * a.info_words;
+    for (int ow = lane; ow < a.info_words; ow += 32) {
+        uint32_t word = 0u;
+        for (int bb = 0; bb < 32; ++bb) {
+            const int j = ow * 32 + bb;
+            if (j < a.Kmsg) {
+                const int p = __ldg(a.msg_pos + j);
+                word |= ((u[p >> 5] >> (p & 31)) & 1u) << bb;
+            }
+        }
+        orow[ow] = word;
+    }
+    __syncwarp();
+}
+
+// ---- stack and snapshot bookkeeping (plain inline functions: the stack
+// stays in registers) ----
+
+// insert candidates 0..nc-1 in order (reading R11): free slots first, all at
+// once, then one by one, each replacing the worst entry (largest pm, ties:
+// oldest) only if its pm is strictly smaller
+__device__ __forceinline__ void insert_cands(Stack &st, int &count, const Cands &c, float pm, uint32_t meta,
+                                             uint32_t base, uint32_t slot, int D, int lane) {
+    const int nfree = D - count;
+    const int nb = c.nc < nfree ? c.nc : nfree;
+    if (nb > 0) {
+        const bool f0 = st.pm[0] == EMPTY && slot_exists(0, lane, D);
+        const bool f1 = st.pm[1] == EMPTY && slot_exists(1, lane, D);
+        const uint32_t b0 = __ballot_sync(FULL, f0), b1 = __ballot_sync(FULL, f1);
+        const uint32_t lt = (1u << lane) - 1u;
+        const int r0 = __popc(b0 & lt);
+        const int r1 = __popc(b0) + __popc(b1 & lt);
+        if (f0 && r0 < nb) {
+            st.pm[0] = __float_as_uint(__fadd_rn(pm, c.delta(r0)));
+            st.meta[0] = meta;
+            st.seq[0] = base + uint32_t(c.nc - 1 - r0);
+            st.aux[0] = slot | (c.mask(r0) << 8);
+        }
+        if (f1 && r1 < nb) {
+            st.pm[1] = __float_as_uint(__fadd_rn(pm, c.delta(r1)));
+            st.meta[1] = meta;
+            st.seq[1] = base + uint32_t(c.nc - 1 - r1);
+            st.aux[1] = slot | (c.mask(r1) << 8);
+        }
+        count += nb;
+    }
+    for (int k = nb; k < c.nc; ++k) {
+        const uint32_t pmb = __float_as_uint(__fadd_rn(pm, c.delta(k)));
+        const bool e0 = slot_exists(0, lane, D), e1 = slot_exists(1, lane, D);
+        uint32_t lw = e0 ? st.pm[0] : 0u, ls = e0 ? st.seq[0] : EMPTY;
+        int lj = 0;
+        if (e1 && (st.pm[1] > lw || (st.pm[1] == lw && st.seq[1] < ls))) {
+            lw = st.pm[1];
+            ls = st.seq[1];
+            lj = 1;
+        }
+        const uint32_t gw = __reduce_max_sync(FULL, lw);
+        const uint32_t gs = __reduce_min_sync(FULL, lw == gw ? ls : EMPTY);
+        if (pmb < gw) {
+            const uint32_t bal = __ballot_sync(FULL, lw == gw && ls == gs);
+            if (lane == __ffs(bal) - 1) {
+                if (lj) {
+                    st.pm[1] = pmb;
+                    st.meta[1] = meta;
+                    st.seq[1] = base + uint32_t(c.nc - 1 - k);
+                    st.aux[1] = slot | (c.mask(k) << 8);
+                } else {
+                    st.pm[0] = pmb;
+                    st.meta[0] = meta;
+                    st.seq[0] = base + uint32_t(c.nc - 1 - k);
+                    st.aux[0] = slot | (c.mask(k) << 8);
+                }
+            }
+        }
+    }
+}
+
+// a free snapshot slot among 0 .. D-1 (one always exists: the extended path
+// left the stack, so at most D - 1 snapshots are referenced)
+__device__ __forceinline__ int alloc_snapshot(const Stack &st, int D) {
+    uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (st.pm[j] != EMPTY) {
+            const uint32_t sn = st.aux[j] & 0xFFu;
+            if (sn < 32u) lo |= 1u << sn;
+            else if (sn < 64u) hi |= 1u << (sn - 32u);
+        }
+    }
+    lo = __reduce_or_sync(FULL, lo);
+    hi = __reduce_or_sync(FULL, hi);
+    const uint64_t used = (uint64_t(hi) << 32) | uint64_t(lo);
+    const uint64_t all = (D >= 64) ? ~0ull : ((1ull << D) - 1ull);
+    const uint64_t fr = ~used & all;
+    return fr ? (__ffsll((long long)fr) - 1) : -1;
+}
+
+__device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int slot, int nbits, uint32_t m01,
+                                               uint32_t m23, int s, int lam) {
+    uint32_t *sp = w.scr + size_t(slot) * SW;
+    const int nw = min(W, (nbits + 31) >> 5);
+    for (int k = w.lane; k < nw; k += 32) sp[k] = w.beta[k];
+    if (w.lane == 0) {
+        sp[W] = m01;
+        sp[W + 1] = m23;
+        sp[W + 2] = uint32_t(s);
+        sp[W + 3] = uint32_t(lam);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b) {
     const int lane = w.lane;
     const int N = a.N, W = a.W, D = a.D, n = a.n;
     const int SW = a.snap_words;
 
+    PT_INIT
     for (int i = lane; i < a.nbranch; i += 32) w.cnt[i] = 0;
     for (int i = lane; i < W; i += 32) w.beta[i] = 0u;
     __syncwarp();
@@ -282,7 +563,10 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
     bool beta_dirty = false;     // working beta replaced since that expansion
     uint32_t applied = 0;        // flips applied on top of the latest snapshot
     int cm[4] = {0, 0, 0, 0};
-    int cs = 0, clam = 0;
+    int cs = 0, clam = n;        // node of the latest expansion
+    // alpha stages valid_lo .. n-1 hold the spine of node (clam, cs),
+    // computed from the working beta's prefix (n: none valid)
+    int cur_lo = n, valid_lo = n;
 
     int crc_fails = 0;
     bool have_first = false;
@@ -290,86 +574,6 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
     int status = POLAR_TIMEOUT;
     float out_pm = __int_as_float(0x7f800000);
     int out_src = 0;  // 0: zeros, 1: working beta, 2: first complete path
-
-    // insert one candidate under the stack rules (reading R11)
-    auto insert = [&](uint32_t pmb, uint32_t meta, uint32_t seq, uint32_t aux) {
-        ops += a.stack_cost;
-        if (count < D) {
-            int j = 0;
-            uint32_t bal = __ballot_sync(FULL, st.pm[0] == EMPTY && slot_exists(0, lane, D));
-            if (bal == 0u) {
-                j = 1;
-                bal = __ballot_sync(FULL, st.pm[1] == EMPTY && slot_exists(1, lane, D));
-            }
-            const int l = __ffs(bal) - 1;
-            if (lane == l) {
-                st.pm[j] = pmb;
-                st.meta[j] = meta;
-                st.seq[j] = seq;
-                st.aux[j] = aux;
-            }
-            ++count;
-        } else {
-            // worst = largest pm, ties: oldest (smallest seq)
-            uint32_t k0 = slot_exists(0, lane, D) ? st.pm[0] : 0u;
-            uint32_t k1 = slot_exists(1, lane, D) ? st.pm[1] : 0u;
-            uint32_t lw = k0, ls = st.seq[0];
-            int lj = 0;
-            if (k1 > lw || (k1 == lw && slot_exists(1, lane, D) && st.seq[1] < ls)) {
-                lw = k1;
-                ls = st.seq[1];
-                lj = 1;
-            }
-            if (!slot_exists(0, lane, D) && !slot_exists(1, lane, D)) {
-                lw = 0u;
-                ls = EMPTY;
-            }
-            const uint32_t gw = __reduce_max_sync(FULL, lw);
-            const uint32_t gs = __reduce_min_sync(FULL, lw == gw ? ls : EMPTY);
-            if (pmb < gw) {  // strictly better than the worst: replace it
-                const uint32_t bal = __ballot_sync(FULL, lw == gw && ls == gs);
-                const int l = __ffs(bal) - 1;
-                if (lane == l) {
-                    st.pm[lj] = pmb;
-                    st.meta[lj] = meta;
-                    st.seq[lj] = seq;
-                    st.aux[lj] = aux;
-                }
-            }
-        }
-    };
-
-    // a free snapshot slot among 0 .. D-1 (one always exists: the extended
-    // path left the stack, so at most D - 1 snapshots are referenced)
-    auto alloc_snapshot = [&]() -> int {
-        uint32_t lo = 0u, hi = 0u;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            if (st.pm[j] != EMPTY) {
-                const uint32_t sn = st.aux[j] & 0xFFu;
-                if (sn < 32u) lo |= 1u << sn;
-                else if (sn < 64u) hi |= 1u << (sn - 32u);
-            }
-        }
-        lo = __reduce_or_sync(FULL, lo);
-        hi = __reduce_or_sync(FULL, hi);
-        uint64_t used = (uint64_t(hi) << 32) | uint64_t(lo);
-        const uint64_t all = (D >= 64) ? ~0ull : ((1ull << D) - 1ull);
-        const uint64_t fr = ~used & all;
-        return fr ? (__ffsll((long long)fr) - 1) : -1;
-    };
-
-    auto write_snapshot = [&](int slot, int nbits, uint32_t m01, uint32_t m23, int s, int lam) {
-        uint32_t *sp = w.scr + size_t(slot) * SW;
-        const int nw = min(W, (nbits + 31) >> 5);
-        for (int k = lane; k < nw; k += 32) sp[k] = w.beta[k];
-        if (lane == 0) {
-            sp[W] = m01;
-            sp[W + 1] = m23;
-            sp[W + 2] = uint32_t(s);
-            sp[W + 3] = uint32_t(lam);
-        }
-    };
 
     int iter = 0;
     for (; iter < a.max_iter; ++iter) {
@@ -408,11 +612,9 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
         --count;
         ++n_iter;
         ops += a.stack_cost;
-        const int p_len = int(p_meta & 0xFFFFu);
         const int p_sched = int(p_meta >> 16);
         const uint32_t p_snap = p_aux & 0xFFu;
         const uint32_t p_mask = (p_aux >> 8) & 0x1Fu;
-        (void)p_len;
         if (p_snap != NOSNAP && p_snap >= uint32_t(D)) {  // never produced; guards the scratch index
             status = POLAR_TIMEOUT;
             break;
@@ -421,9 +623,11 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
             status = POLAR_TIMEOUT;
             break;
         }
+        PT(PH_POP)
 
         // ---- restore the path's beta array ----
-        bool need_restore = false;
+        bool switched = false;
+        int div = 0;  // first bit where the popped path's beta differs from the working one
         if (p_snap == cur_snap) {
             if (beta_dirty) {
                 const uint32_t *sp = w.scr + size_t(cur_snap) * SW;
@@ -431,35 +635,39 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
                 __syncwarp();
                 applied = 0u;
                 beta_dirty = false;
+                valid_lo = cur_lo;
             }
             w.apply_flips(applied ^ p_mask, cm, cs, clam);
             applied = p_mask;
         } else {  // path switch (Sec. 3.3)
+            switched = true;
             ++n_switch;
             ops += uint32_t(W);
             const uint32_t *sp = w.scr + size_t(p_snap) * SW;
-            for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
             const uint32_t m01 = sp[W], m23 = sp[W + 1];
             const int ss = int(sp[W + 2]), slam = int(sp[W + 3]);
+            uint32_t dl = EMPTY;
+            for (int k = lane; k < W; k += 32) {
+                const uint32_t nv = sp[k];
+                const uint32_t x = nv ^ w.beta[k];
+                w.beta[k] = nv;
+                if (x && dl == EMPTY) dl = uint32_t(32 * k + __ffs(x) - 1);
+            }
+            dl = __reduce_min_sync(FULL, dl);
+            div = int(min(dl, uint32_t(ss)));  // the flips below only touch [ss, ...)
             const int mm[4] = {int(m01 & 0xFFFFu), int(m01 >> 16), int(m23 & 0xFFFFu), int(m23 >> 16)};
             __syncwarp();
             w.apply_flips(p_mask, mm, ss, slam);
-            need_restore = true;
             beta_dirty = true;
         }
+        PT(PH_BETA)
 
         if (p_sched == a.nops) {  // a complete path
+            if (switched) valid_lo = n;  // beta replaced, alpha left as it was
             bool pass = true;
             if (a.crc) {
                 ops += uint32_t(a.crc) * uint32_t(W);
-                uint32_t syn = 0u;
-                for (int r = 0; r < a.crc; ++r) {
-                    uint32_t par = 0u;
-                    for (int k = lane; k < W; k += 32) par ^= __popc(w.beta[k] & __ldg(a.crc_rows + size_t(r) * W + k));
-                    syn |= (par & 1u) << r;
-                }
-                syn = __reduce_xor_sync(FULL, syn);
-                pass = (syn == 0u);
+                pass = crc_ok(a, w.beta, lane);
             }
             if (pass) {
                 status = POLAR_OK;
@@ -481,29 +689,39 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
                 out_src = 2;
                 break;
             }
+            PT(PH_DONE)
             continue;
         }
 
-        // ---- recompute the alpha spine after a switch (Alg. calp) ----
-        if (need_restore) {
+        // ---- alpha after a switch (Alg. calp): recompute the spine from the
+        // channel, except the top stages the popped path shares with the
+        // spine held now (same node, identical beta before the node) ----
+        if (switched) {
             const uint32_t tgt = __ldg(&a.ops[p_sched].z);
             if (tgt != NO_TARGET) {
                 const int lam_d = int(tgt & 0xFFu);
                 const int s_d = int(tgt >> 8);
-                ops += 2u * uint32_t(N - (1 << lam_d));
-                for (int lam = n - 1; lam >= lam_d; --lam) {
+                ops += 2u * uint32_t(N - (1 << lam_d));  // counted as the full recompute
+                int lam = n - 1;
+                while (lam >= lam_d && lam >= valid_lo && (s_d >> lam) == (cs >> lam) && div >= ((s_d >> lam) << lam))
+                    --lam;
+                for (; lam >= lam_d; --lam) {
                     const int sl = (s_d >> lam) << lam;
                     if ((s_d >> lam) & 1) w.op_g(lam, sl);
                     else w.op_f(lam);
                 }
             }
         }
+        PT(PH_ALPHA)
 
         // ---- walk the schedule to the next branching node ----
         float pm = __uint_as_float(p_pmb);
         int t = p_sched;
+        const uint4 *opsv = reinterpret_cast<const uint4 *>(a.ops);
+        uint4 nxt = __ldg(opsv + min(t, a.nops - 1));
         for (; t < a.nops; ++t) {
-            const uint4 op = __ldg(reinterpret_cast<const uint4 *>(a.ops) + t);
+            const uint4 op = nxt;
+            if (t + 1 < a.nops) nxt = __ldg(opsv + t + 1);
             const uint32_t code = op.x & 0xFFu;
             const int lam = int((op.x >> 8) & 0xFFu);
             const int s = int(op.y);
@@ -511,35 +729,44 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
             if (code == OP_F) {
                 w.op_f(lam);
                 ops += 2u << lam;
+                PT(PH_FG)
             } else if (code == OP_G) {
                 w.op_g(lam, s);
                 ops += 2u << lam;
+                PT(PH_FG)
             } else if (code == OP_COMB) {
                 w.op_comb(lam, s);
                 ops += (lam < 5) ? 1u : (1u << (lam - 5));
+                PT(PH_COMB)
             } else {  // Rate-0 node or frozen leaf: beta = 0, PM += sum HD(a)|a|
-                const float pen = w.halving_sum(w.stage(lam), lam, 1);
+                const float pen = w.node_sum(lam, 1);
                 w.set_range(lam, s, 0u);
                 pm = __fadd_rn(pm, pen);
                 ops += (2u << lam) + 1u;
+                PT(PH_R0)
             }
         }
         ++n_exp;
         if (t == a.nops) {  // the path is complete: push it
-            const int slot = alloc_snapshot();
+            const int slot = alloc_snapshot(st, D);
             if (slot < 0) break;
-            write_snapshot(slot, N, 0u, 0u, 0, 0);
-            __syncwarp();
+            write_snapshot(w, W, SW, slot, N, 0u, 0u, 0, 0);
             cur_snap = uint32_t(slot);
             applied = 0u;
             beta_dirty = false;
-            ops += 1u;
-            insert(__float_as_uint(pm), uint32_t(N) | (uint32_t(a.nops) << 16), seq_next++, uint32_t(slot));
+            cur_lo = valid_lo = n;
+            clam = n;
+            cs = 0;
+            ops += 1u + a.stack_cost;
+            Cands one{1, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
+            insert_cands(st, count, one, pm, uint32_t(N) | (uint32_t(a.nops) << 16), seq_next, uint32_t(slot), D, lane);
+            seq_next += 1u;
+            PT(PH_DONE)
             continue;
         }
 
         // ---- branching node: visit counter and L-prune (Sec. 2.2.5) ----
-        const uint4 op = __ldg(reinterpret_cast<const uint4 *>(a.ops) + t);
+        const uint4 op = __ldg(opsv + t);
         const uint32_t code = op.x & 0xFFu;
         const int lam = int((op.x >> 8) & 0xFFu);
         const int s = int(op.y);
@@ -559,70 +786,55 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
             }
             count -= removed;
         }
+        PT(PH_PRUNE)
 
         // ---- node candidates (Sec. 2.2.4 and readings R7-R9) ----
-        const float *A = w.stage(lam);
-        float delta[8];
-        uint32_t masks[8];
-        int nc = 0;
+        Cands cd{0, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
         int m[4] = {0, 0, 0, 0};
         if (code == OP_LEAF1) {
-            const float x = A[0];
-            w.write_hd(A, 0, s);
-            delta[0] = 0.0f;
-            masks[0] = 0u;
-            delta[1] = fabsf(x);
-            masks[1] = 1u;
-            nc = 2;
+            cd.mag[0] = fabsf(w.stage(0)[0]);
+            w.node_hd(0, s);
+            cd.nc = 2;
+            cd.masks = LEAF1_MASKS;
             ops += 4u;
         } else if (code == OP_REP) {
-            const float S = w.halving_sum(A, lam, 0);
-            const uint32_t bbit = S < 0.0f ? 1u : 0u;
-            const float p0 = w.halving_sum(A, lam, bbit ? 2 : 1);
+            float S, p0;
+            uint32_t bbit;
+            if (len <= 32) {
+                float pz, po;
+                w.rep_sums(lam, S, pz, po);
+                bbit = S < 0.0f ? 1u : 0u;
+                p0 = bbit ? po : pz;
+            } else {
+                S = w.node_sum(lam, 0);
+                bbit = S < 0.0f ? 1u : 0u;
+                p0 = w.node_sum(lam, bbit ? 2 : 1);
+            }
             w.set_range(lam, s, bbit);
-            delta[0] = p0;
-            masks[0] = 0u;
-            delta[1] = __fadd_rn(p0, fabsf(S));
-            masks[1] = FLIP_ALL;
-            nc = 2;
+            cd.nc = 2;
+            cd.rep = true;
+            cd.rep0 = p0;
+            cd.rep1 = __fadd_rn(p0, fabsf(S));
             ops += 4u * uint32_t(len) + 3u;
         } else if (code == OP_R1) {
-            float mag[4];
-            w.write_hd(A, lam, s);
-            w.least_k(A, lam, 2, m, mag);
-            delta[0] = 0.0f;
-            masks[0] = 0u;
-            delta[1] = mag[0];
-            masks[1] = 1u;
-            delta[2] = mag[1];
-            masks[2] = 2u;
-            delta[3] = __fadd_rn(mag[0], mag[1]);
-            masks[3] = 3u;
-            nc = 4;
+            w.node_hd(lam, s);
+            w.node_least(lam, 2, m, cd.mag);
+            cd.nc = 4;
+            cd.masks = R1_MASKS;
             ops += 6u * uint32_t(len) + 5u;
         } else {  // OP_SPC
-            float mag[4];
-            const uint32_t q = w.write_hd(A, lam, s);
-            w.least_k(A, lam, 4, m, mag);
-            for (uint32_t mk = 0; mk < 16u; ++mk) {
-                const uint32_t pc = uint32_t(__popc(mk));
-                if ((pc & 1u) != q) continue;
-                float d = 0.0f;
-                for (int j = 0; j < 4; ++j)
-                    if ((mk >> j) & 1u) d = __fadd_rn(d, mag[j]);
-                delta[nc] = d;
-                masks[nc] = mk;
-                ++nc;
-                ops += 1u + (pc > 1u ? pc - 1u : 0u);
-            }
-            ops += 10u * uint32_t(len);
+            const uint32_t q = w.node_hd(lam, s);
+            w.node_least(lam, 4, m, cd.mag);
+            cd.nc = 8;
+            cd.masks = q ? SPC_MASKS_ODD : SPC_MASKS_EVEN;
+            ops += 10u * uint32_t(len) + (q ? 16u : 17u);
         }
+        PT(PH_NODE)
 
-        const int slot = alloc_snapshot();
+        const int slot = alloc_snapshot(st, D);
         if (slot < 0) break;
-        write_snapshot(slot, s + len, uint32_t(m[0]) | (uint32_t(m[1]) << 16), uint32_t(m[2]) | (uint32_t(m[3]) << 16),
-                       s, lam);
-        __syncwarp();
+        write_snapshot(w, W, SW, slot, s + len, uint32_t(m[0]) | (uint32_t(m[1]) << 16),
+                       uint32_t(m[2]) | (uint32_t(m[3]) << 16), s, lam);
         cur_snap = uint32_t(slot);
         applied = 0u;
         beta_dirty = false;
@@ -632,15 +844,15 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
         cm[3] = m[3];
         cs = s;
         clam = lam;
-        const uint32_t base = seq_next;
-        seq_next += uint32_t(nc);
-        const uint32_t meta = uint32_t(s + len) | (uint32_t(t + 1) << 16);
-        for (int k = 0; k < nc; ++k)
-            insert(__float_as_uint(__fadd_rn(pm, delta[k])), meta, base + uint32_t(nc - 1 - k),
-                   uint32_t(slot) | (masks[k] << 8));
+        cur_lo = valid_lo = lam;
+        PT(PH_SNAP)
+        ops += uint32_t(cd.nc) * a.stack_cost;
+        insert_cands(st, count, cd, pm, uint32_t(s + len) | (uint32_t(t + 1) << 16), seq_next, uint32_t(slot), D, lane);
+        seq_next += uint32_t(cd.nc);
+        PT(PH_INSERT)
     }
 
-    // ---- output: re-encode the codeword estimate, read the message ----
+    // ---- output ----
     if (out_src == 2) {
         const uint32_t *sp = w.scr + size_t(D) * SW;
         for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
@@ -649,34 +861,7 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
     }
     __syncwarp();
     ops += uint32_t(n) * uint32_t(W);
-    uint32_t *u = w.beta;
-    for (int k = lane; k < W; k += 32) {
-        uint32_t x = u[k];
-        if (N > 1) x ^= (x >> 1) & 0x55555555u;
-        if (N > 2) x ^= (x >> 2) & 0x33333333u;
-        if (N > 4) x ^= (x >> 4) & 0x0F0F0F0Fu;
-        if (N > 8) x ^= (x >> 8) & 0x00FF00FFu;
-        if (N > 16) x ^= (x >> 16) & 0x0000FFFFu;
-        u[k] = x;
-    }
-    __syncwarp();
-    for (int hw = 1; hw < W; hw <<= 1) {
-        for (int k = lane; k < W; k += 32)
-            if (!(k & hw)) u[k] ^= u[k + hw];
-        __syncwarp();
-    }
-    uint32_t *orow = a.info_out + size_t(b) * a.info_words;
-    for (int ow = lane; ow < a.info_words; ow += 32) {
-        uint32_t word = 0u;
-        for (int bb = 0; bb < 32; ++bb) {
-            const int j = ow * 32 + bb;
-            if (j < a.Kmsg) {
-                const int p = __ldg(a.msg_pos + j);
-                word |= ((u[p >> 5] >> (p & 31)) & 1u) << bb;
-            }
-        }
-        orow[ow] = word;
-    }
+    write_output(a, w.beta, b, lane);
     if (lane == 0) {
         if (status == POLAR_TIMEOUT) out_pm = __int_as_float(0x7f800000);
         a.pm_out[b] = out_pm;
@@ -690,6 +875,8 @@ __device__ void decode_frame(const Args &a, Warp &w, unsigned b) {
         }
     }
     __syncwarp();
+    PT(PH_OUT)
+    PT_FLUSH
 }
 
 __global__ void __launch_bounds__(128) scs_decode_kernel(Args a) {
@@ -741,6 +928,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     while ((1 << lg) < D) ++lg;
     a.stack_cost = 2u * uint32_t(lg < 1 ? 1 : lg);
     a.warp_smem = ((4 * p->N + 4 * p->W + p->nbranch) + 15) & ~15;
+    a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
 
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -882,6 +1070,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     while ((1 << lg) < D) ++lg;
     a.stack_cost = 2u * uint32_t(lg < 1 ? 1 : lg);
     a.warp_smem = ((4 * p->N + 4 * p->W + p->nbranch) + 15) & ~15;
+    a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
 
     // as many resident warps as the static scratch holds (the kernel is
     // persistent and claims frames dynamically, so fewer warps only cost speed)
@@ -924,3 +1113,15 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
 }
 
 }  // namespace polarscs
+
+#ifdef POLAR_PHASE_TIMERS
+// debug builds only: read (and optionally clear) the per-phase cycle sums
+extern "C" int polar_phase_cycles(unsigned long long *out, int reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, polarscs::g_phase_cycles, sizeof(unsigned long long) * polarscs::PH_N);
+    if (e == cudaSuccess && reset) {
+        static const unsigned long long zeros[polarscs::PH_N] = {};
+        e = cudaMemcpyToSymbol(polarscs::g_phase_cycles, zeros, sizeof(zeros));
+    }
+    return e == cudaSuccess ? polarscs::PH_N : -3;
+}
+#endif
