@@ -147,6 +147,45 @@ int scs_decode_batch(const polar_plan *plan, const float *d_llr, int B, int D, i
 int scs_decode_batch_noalloc(const polar_plan *plan, const float *d_llr, int B, int D, int L, uint32_t *d_info,
                              float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream);
 
+/* ---- Mixed batches (one persistent launch for frames of different codes) ----
+ * Not a construct of the paper: a batching form of the same decoder.  Every
+ * frame is decoded exactly as scs_decode_batch would decode it alone with its
+ * own plan, D and L. */
+typedef struct polar_plan_set polar_plan_set;
+
+/* Group 1..64 plans (not copied: they must outlive the set).  Host only.
+ * Errors: POLAR_EINVAL, POLAR_ELIMIT (a plan with N > 8192), POLAR_ENOMEM. */
+int polar_plan_set_create(const polar_plan *const *plans, int nplans, polar_plan_set **out);
+void polar_plan_set_destroy(polar_plan_set *set);
+
+/* Decode B frames of mixed codes in one persistent launch.
+ *  d_frames   device, [B, 4] int32 per frame: plan index in the set, D
+ *             (1..Dmax), L (1..255), unused; 16-byte aligned
+ *  Dmax       largest D of the batch (<= 64); sizes the scratch
+ *  d_llr      device float32 LLRs of all frames, packed; frame b's N values
+ *             start at d_llr[d_llr_off[b]] (16-byte aligned starts are read
+ *             with vector loads)
+ *  d_info     device packed message words; frame b's ceil(K_msg/32) words
+ *             start at d_info[d_info_off[b]]
+ *  d_pm, d_status, d_stats as in scs_decode_batch, indexed by frame.  A frame
+ *  whose descriptor is invalid (bad plan index, D or L) gets status 3 and
+ *  pm = +inf, and nothing else of it is read or written.
+ * The set's device tables are made on the first call on a device (make that
+ * call before any stream capture; later calls can be captured in a CUDA
+ * graph).  Asynchronous on stream. */
+int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_frames, int B, int Dmax, const float *d_llr,
+                     const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
+                     int8_t *d_status, uint32_t *d_stats, void *stream);
+
+/* Autotuner for scs_decode_mixed: decodes the given batch (same arguments)
+ * with every combination of 1, 2 or 4 warps (frames in flight) per block and
+ * 1, 4 or 16 frames claimed per atomic, times each on the stream with CUDA
+ * events (synchronising), and keeps the fastest in the set for later calls.
+ * *wpb_out and *chunk_out (optional) receive the choice. */
+int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, int B, int Dmax, const float *d_llr,
+                   const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
+                   int8_t *d_status, void *stream, int *wpb_out, int *chunk_out);
+
 /* Decode one frame held in host memory (synchronous), fast nodes on:
  * llr N floats in, info_out K - crc bytes (one bit per byte) out, *pm_out the
  * final path metric.  Returns the frame status (>= 0) or an error (< 0). */

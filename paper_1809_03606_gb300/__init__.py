@@ -26,6 +26,7 @@ OP_NAMES = {0: "alpha", 1: "beta", 2: "R0", 3: "R1", 4: "REP", 5: "SPC", 6: "lea
 EXPORTED = (
     "polar_construct", "polar_plan_create", "polar_plan_destroy", "polar_plan_schedule", "polar_encode_batch",
     "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info", "scs_decode_batch_noalloc",
+    "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
 )
 
 _lock = threading.Lock()
@@ -68,6 +69,11 @@ def load(build_if_missing: bool = False):
         lib.scs_decode.argtypes = [vp, i32, i32, vp, i32, i32, i32, vp, vp]
         lib.scs_decode_batch_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
         lib.polar_device_info.argtypes = [vp, vp, vp]
+        lib.polar_plan_set_create.argtypes = [vp, i32, C.POINTER(vp)]
+        lib.polar_plan_set_destroy.argtypes = [vp]
+        lib.polar_plan_set_destroy.restype = None
+        lib.scs_decode_mixed.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.scs_tune_mixed.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib = lib
         return lib
 
@@ -216,6 +222,116 @@ def decode(plan: Plan, llr, D: int, L: int, with_stats: bool = False, stream=Non
     stats = torch.empty((B, 4), dtype=torch.int32, device=dev) if with_stats else None
     scs_decode_batch(plan, llr, D, L, info, pm, status, stats, stream)
     return (info, pm, status, stats) if with_stats else (info, pm, status)
+
+
+# ------------------------------------------------------------- mixed batches
+class PlanSet:
+    """Owner of a ``polar_plan_set*``: plans decoded together by index."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)  # kept alive: the set refers to them
+        arr = (C.c_void_p * len(self.plans))(*[pl.handle.value for pl in self.plans])
+        h = C.c_void_p()
+        _check("polar_plan_set_create", load().polar_plan_set_create(C.cast(arr, C.c_void_p), len(self.plans), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            load().polar_plan_set_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def polar_plan_set_create(plans) -> PlanSet:
+    return PlanSet(plans)
+
+
+def polar_plan_set_destroy(pset: PlanSet) -> None:
+    pset.close()
+
+
+def _mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status):
+    import torch
+
+    B = frames.shape[0]
+    return (pset.handle, _dev_ptr(frames, torch.int32, "frames", (B, 4)), B, int(Dmax),
+            _dev_ptr(llr, torch.float32, "llr"), _dev_ptr(llr_off, torch.int64, "llr_off", (B,)),
+            _dev_ptr(info, torch.int32, "info"), _dev_ptr(info_off, torch.int64, "info_off", (B,)),
+            _dev_ptr(pm, torch.float32, "pm", (B,)), _dev_ptr(status, torch.int8, "status", (B,)))
+
+
+def scs_decode_mixed(pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_off, pm, status, stats=None,
+                     stream=None) -> None:
+    """Decode a packed batch of frames of different codes in one launch (see polarscs.h)."""
+    import torch
+
+    B = frames.shape[0]
+    _check("scs_decode_mixed", load().scs_decode_mixed(
+        *_mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status),
+        None if stats is None else _dev_ptr(stats, torch.int32, "stats", (B, 4)), _stream_ptr(stream)))
+
+
+def scs_tune_mixed(pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_off, pm, status, stream=None):
+    """Run the native autotuner on this batch; returns (warps per block, frames per claim)."""
+    w, c = C.c_int(0), C.c_int(0)
+    _check("scs_tune_mixed", load().scs_tune_mixed(
+        *_mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status), _stream_ptr(stream),
+        C.byref(w), C.byref(c)))
+    return w.value, c.value
+
+
+class MixedBatch:
+    """Device buffers of a mixed batch: frames (plan index, D, L) with their
+    packed LLRs and output slots.  Built from host arrays (marshalling only)."""
+
+    def __init__(self, pset: PlanSet, plan_idx, D, L, llr_rows, device="cuda"):
+        import torch
+
+        plan_idx = np.asarray(plan_idx, np.int32)
+        B = plan_idx.size
+        Ns = np.array([pset.plans[i].N for i in plan_idx], np.int64)
+        words = np.array([pset.plans[i].msg_words for i in plan_idx], np.int64)
+        self.B = B
+        self.llr_off_np = np.concatenate([[0], np.cumsum(Ns)[:-1]]).astype(np.int64)
+        self.info_off_np = np.concatenate([[0], np.cumsum(words)[:-1]]).astype(np.int64)
+        fr = np.zeros((B, 4), np.int32)
+        fr[:, 0] = plan_idx
+        fr[:, 1] = np.asarray(D, np.int32)
+        fr[:, 2] = np.asarray(L, np.int32)
+        self.Dmax = int(fr[:, 1].max()) if B else 1
+        self.frames = torch.from_numpy(fr).to(device)
+        if isinstance(llr_rows, np.ndarray) and llr_rows.ndim == 1:
+            flat = llr_rows.astype(np.float32, copy=False)
+        else:
+            flat = np.concatenate([np.asarray(r, np.float32) for r in llr_rows]) if B else np.zeros(0, np.float32)
+        self.llr = torch.from_numpy(flat).to(device)
+        self.llr_off = torch.from_numpy(self.llr_off_np).to(device)
+        self.info_off = torch.from_numpy(self.info_off_np).to(device)
+        self.info = torch.zeros(int(words.sum()) if B else 1, dtype=torch.int32, device=device)
+        self.pm = torch.empty(B, dtype=torch.float32, device=device)
+        self.status = torch.empty(B, dtype=torch.int8, device=device)
+        self.words = words
+
+    def decode(self, pset: PlanSet, stats=None, stream=None) -> None:
+        scs_decode_mixed(pset, self.frames, self.Dmax, self.llr, self.llr_off, self.info, self.info_off, self.pm,
+                         self.status, stats, stream)
+
+    def tune(self, pset: PlanSet, stream=None):
+        return scs_tune_mixed(pset, self.frames, self.Dmax, self.llr, self.llr_off, self.info, self.info_off, self.pm,
+                              self.status, stream)
+
+    def message_words(self, b: int) -> np.ndarray:
+        lo = int(self.info_off_np[b])
+        return self.info[lo:lo + int(self.words[b])].cpu().numpy()
 
 
 def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, D: int, L: int, crc: int = 0):

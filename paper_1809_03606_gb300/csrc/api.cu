@@ -4,8 +4,10 @@
 // the host except argument validation and table building.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <new>
 #include <cstring>
 #include <vector>
 
@@ -19,6 +21,10 @@ int launch_polar_encode(const polar_plan *p, const DeviceTables *dt, const uint3
                         cudaStream_t stream);
 int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
                               float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream);
+int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, int B, int Dmax, const float *d_llr,
+                            const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off, float *d_pm,
+                            int8_t *d_status, uint32_t *d_stats, cudaStream_t stream, int wpb_req, int chunk_req);
+void free_set_device(polar_plan_set *set);
 
 // Per-call scratch comes from the device's default stream-ordered pool.  By
 // default that pool returns memory to the driver at every synchronisation,
@@ -122,6 +128,105 @@ extern "C" int scs_decode_batch_noalloc(const polar_plan *p, const float *d_llr,
     if (p->N > POLAR_MAX_N_GPU || D > POLAR_MAX_D_GPU || L > POLAR_MAX_L_GPU) return POLAR_ELIMIT;
     if (B == 0) return 0;
     return launch_scs_decode_noalloc(p, d_llr, B, D, L, d_info, d_pm, d_status, d_stats, cudaStream_t(stream));
+}
+
+extern "C" int polar_plan_set_create(const polar_plan *const *plans, int nplans, polar_plan_set **out) {
+    if (!out || !plans || nplans < 1 || nplans > 64) return POLAR_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < nplans; ++i) {
+        if (!plans[i]) return POLAR_EINVAL;
+        if (plans[i]->N > POLAR_MAX_N_GPU) return POLAR_ELIMIT;
+    }
+    polar_plan_set *set = new (std::nothrow) polar_plan_set();
+    if (!set) return POLAR_ENOMEM;
+    for (int i = 0; i < nplans; ++i) {
+        set->plans.push_back(plans[i]);
+        set->Nmax = std::max(set->Nmax, plans[i]->N);
+        set->Wmax = std::max(set->Wmax, plans[i]->W);
+        set->nbranch_max = std::max(set->nbranch_max, plans[i]->nbranch);
+    }
+    *out = set;
+    return 0;
+}
+
+extern "C" void polar_plan_set_destroy(polar_plan_set *set) {
+    if (!set) return;
+    free_set_device(set);
+    delete set;
+}
+
+static int check_mixed(const polar_plan_set *set, const int32_t *d_frames, int B, int Dmax, const float *d_llr,
+                       const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
+                       int8_t *d_status) {
+    if (!set || B < 0 || Dmax < 1) return POLAR_EINVAL;
+    if (B > 0 && (!d_frames || !d_llr || !d_llr_off || !d_info || !d_info_off || !d_pm || !d_status)) return POLAR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_frames) & 15u) != 0u) return POLAR_EINVAL;
+    if (Dmax > POLAR_MAX_D_GPU) return POLAR_ELIMIT;
+    return 0;
+}
+
+extern "C" int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_frames, int B, int Dmax,
+                                const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info,
+                                const int64_t *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
+                                void *stream) {
+    int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
+    if (rc || B == 0) return rc;
+    return launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), B, Dmax, d_llr,
+                                   reinterpret_cast<const long long *>(d_llr_off), d_info,
+                                   reinterpret_cast<const long long *>(d_info_off), d_pm, d_status, d_stats,
+                                   cudaStream_t(stream), 0, 0);
+}
+
+extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, int B, int Dmax, const float *d_llr,
+                              const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
+                              int8_t *d_status, void *stream, int *wpb_out, int *chunk_out) {
+    int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
+    if (rc) return rc;
+    if (B == 0) return POLAR_EINVAL;
+    cudaStream_t s = cudaStream_t(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_status(e);
+    }
+    static const int kWpb[] = {1, 2, 4};
+    static const int kChunk[] = {1, 4, 16};
+    float best = -1.0f;
+    int bw = 4, bc = 1;
+    for (int wi = 0; wi < 3 && rc == 0; ++wi) {
+        for (int ci = 0; ci < 3 && rc == 0; ++ci) {
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && rc == 0; ++rep) {  // first run warms up, the second is timed
+                cudaEventRecord(e0, s);
+                rc = launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), B, Dmax, d_llr,
+                                             reinterpret_cast<const long long *>(d_llr_off), d_info,
+                                             reinterpret_cast<const long long *>(d_info_off), d_pm, d_status, nullptr,
+                                             s, kWpb[wi], kChunk[ci]);
+                cudaEventRecord(e1, s);
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) rc = cuda_status(e);
+                if (rc == 0) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rc == 0 && (best < 0.0f || ms < best)) {
+                best = ms;
+                bw = kWpb[wi];
+                bc = kChunk[ci];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> g(set->mu);
+        set->tuned_wpb = bw;
+        set->tuned_chunk = bc;
+    }
+    if (wpb_out) *wpb_out = bw;
+    if (chunk_out) *chunk_out = bc;
+    return 0;
 }
 
 extern "C" int polar_encode_batch(const polar_plan *p, const uint32_t *d_msg, int B, uint32_t *d_codeword,

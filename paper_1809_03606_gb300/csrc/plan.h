@@ -62,6 +62,17 @@ struct polar_plan {
     mutable polarscs::DeviceTables dev;
 };
 
+// A set of plans decoded together by scs_decode_mixed (frames name their
+// plan by index).  Device state is made on first use and serves one device.
+struct polar_plan_set {
+    std::vector<const polar_plan *> plans;
+    int Nmax = 0, Wmax = 0, nbranch_max = 0;
+    mutable std::mutex mu;
+    mutable int device = -1;
+    mutable void *d_codes = nullptr;  // device array of the kernels' code records
+    mutable int tuned_wpb = 0, tuned_chunk = 0;  // 0: not tuned yet
+};
+
 namespace polarscs {
 
 int validate_code(int N, int K, const uint8_t *frozen, int crc);

@@ -45,25 +45,40 @@ constexpr uint32_t SPC_MASKS_ODD = 0xEDB87421u;   // 1,2,4,7,8,11,13,14
 constexpr uint32_t R1_MASKS = 0x3210u;            // Chase-II: none, m1, m2, both
 constexpr uint32_t LEAF1_MASKS = 0x10u;           // decision, flipped decision
 
-struct Args {
-    const float *llr;
-    int B, N, n, W, Kmsg, crc, D, L;
+// One polar code as the kernel sees it: its schedule and tables (device
+// pointers) and sizes.
+struct Code {
     const KOp *ops;
-    int nops, nbranch;
     const uint32_t *crc_rows;
     const uint16_t *msg_pos;
+    int N, n, W, Kmsg, crc, nops, nbranch, info_words;
+    int snap_words;  // words per snapshot slot: W beta words + 4 meta words, padded
+};
+
+constexpr int kMaxCodes = 64;  // codes of one mixed batch (shared-memory table)
+constexpr int kBadFrame = 3;   // status of a mixed-batch frame whose descriptor is invalid
+
+struct Args {
+    Code code;                  // uniform batch: every frame uses this code, D and L
+    int D, L;
+    const Code *codes;          // mixed batch: frame b uses codes[frames[b].x]
+    int ncodes;
+    const int4 *frames;         // mixed: (code index, D, L, unused) per frame
+    const long long *llr_off;   // mixed: index of frame b's first LLR
+    const long long *info_off;  // mixed: index of frame b's first message word
+    int Dmax;                   // mixed: largest D the scratch was sized for
+    const float *llr;
+    int B;
     uint32_t *info_out;
-    int info_words;
     float *pm_out;
     int8_t *status_out;
     uint32_t *stats_out;
     uint32_t *scratch;
-    int snap_words;  // words per snapshot slot: W beta words + 4 meta words, padded
+    long long scratch_stride;   // snapshot words per warp
     unsigned *counter;
-    int max_iter;
-    uint32_t stack_cost;
-    int warp_smem;  // bytes of shared memory per warp
-    int llr_vec;    // the LLR rows are 16-byte aligned: vector loads of the root
+    int warp_smem;              // bytes of shared memory per warp
+    int llr_vec;                // the LLR buffer is 16-byte aligned
+    int chunk;                  // frames claimed per atomic
 };
 
 // Optional per-phase cycle counters (debug builds with -DPOLAR_PHASE_TIMERS):
@@ -103,16 +118,17 @@ __device__ __forceinline__ float pen_transform(float x, int mode) {
 }
 
 struct Warp {
-    const Args &a;
     const int lane;
+    const int n;          // stage of the root
+    const int llr_vec;    // the root may be read with vector loads
     float *alpha;     // shared: stage lambda at alpha + 2^lambda
     uint32_t *beta;   // shared: W words
     uint8_t *cnt;     // shared: visit counters
     uint32_t *scr;    // global: (D + 1) snapshot slots
     const float *root;
 
-    __device__ const float *stage(int lam) const { return lam == a.n ? root : alpha + (1 << lam); }
-    __device__ bool vec_ok(int plam) const { return plam < a.n || a.llr_vec; }
+    __device__ const float *stage(int lam) const { return lam == n ? root : alpha + (1 << lam); }
+    __device__ bool vec_ok(int plam) const { return plam < n || llr_vec; }
 
     // alpha of the even child (lamc) from its parent (Eq. llrcalc, f)
     __device__ void op_f(int lamc) const {
@@ -390,11 +406,11 @@ struct Cands {
 // CRC syndrome of the codeword estimate in beta: zero iff the message's CRC
 // matches (the long division is linear, so the syndrome is a fixed GF(2)
 // matrix applied to the codeword bits)
-__device__ __noinline__ bool crc_ok(const Args &a, const uint32_t *beta, int lane) {
+__device__ __noinline__ bool crc_ok(const Code &c, const uint32_t *beta, int lane) {
     uint32_t syn = 0u;
-    for (int r = 0; r < a.crc; ++r) {
+    for (int r = 0; r < c.crc; ++r) {
         uint32_t par = 0u;
-        for (int k = lane; k < a.W; k += 32) par ^= __popc(beta[k] & __ldg(a.crc_rows + size_t(r) * a.W + k));
+        for (int k = lane; k < c.W; k += 32) par ^= __popc(beta[k] & __ldg(c.crc_rows + size_t(r) * c.W + k));
         syn |= (par & 1u) << r;
     }
     return __reduce_xor_sync(FULL, syn) == 0u;
@@ -402,8 +418,8 @@ __device__ __noinline__ bool crc_ok(const Args &a, const uint32_t *beta, int lan
 
 // output: re-encode the codeword estimate (F is an involution, Sec. 2.2.2)
 // and read the message bits off the information set
-__device__ __noinline__ void write_output(const Args &a, uint32_t *u, unsigned b, int lane) {
-    const int W = a.W, N = a.N;
+__device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *orow, int lane) {
+    const int W = c.W, N = c.N;
     for (int k = lane; k < W; k += 32) {
         uint32_t x = u[k];
         if (N > 1) x ^= (x >> 1) & 0x55555555u;
@@ -419,13 +435,12 @@ __device__ __noinline__ void write_output(const Args &a, uint32_t *u, unsigned b
             if (!(k & hw)) u[k] ^= u[k + hw];
         __syncwarp();
     }
-    uint32_t *orow = a.info_out + size_t(b) * a.info_words;
-    for (int ow = lane; ow < a.info_words; ow += 32) {
+    for (int ow = lane; ow < c.info_words; ow += 32) {
         uint32_t word = 0u;
         for (int bb = 0; bb < 32; ++bb) {
             const int j = ow * 32 + bb;
-            if (j < a.Kmsg) {
-                const int p = __ldg(a.msg_pos + j);
+            if (j < c.Kmsg) {
+                const int p = __ldg(c.msg_pos + j);
                 word |= ((u[p >> 5] >> (p & 31)) & 1u) << bb;
             }
         }
@@ -530,13 +545,16 @@ __device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int
     __syncwarp();
 }
 
-__device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b) {
+__device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Warp &w,
+                                             unsigned b, uint32_t *orow) {
     const int lane = w.lane;
-    const int N = a.N, W = a.W, D = a.D, n = a.n;
-    const int SW = a.snap_words;
+    const int N = c.N, W = c.W, n = c.n;
+    const int SW = c.snap_words;
+    const int max_iter = L * (c.nbranch + 9) + 2;
+    const uint32_t stack_cost = 2u * uint32_t(D > 2 ? 32 - __clz(D - 1) : 1);
 
     PT_INIT
-    for (int i = lane; i < a.nbranch; i += 32) w.cnt[i] = 0;
+    for (int i = lane; i < c.nbranch; i += 32) w.cnt[i] = 0;
     for (int i = lane; i < W; i += 32) w.beta[i] = 0u;
     __syncwarp();
 
@@ -556,7 +574,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
     }
     int count = 1;
     uint32_t seq_next = 1;
-    uint32_t ops = a.stack_cost;  // counted operations (roofline convention)
+    uint32_t ops = stack_cost;  // counted operations (roofline convention)
     uint32_t n_iter = 0, n_switch = 0, n_exp = 0;
 
     uint32_t cur_snap = NOSNAP;  // snapshot of the latest expansion
@@ -576,7 +594,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
     int out_src = 0;  // 0: zeros, 1: working beta, 2: first complete path
 
     int iter = 0;
-    for (; iter < a.max_iter; ++iter) {
+    for (; iter < max_iter; ++iter) {
         if (count == 0) {  // every path deleted (reading R12)
             status = POLAR_CRC_FAIL;
             if (have_first) {
@@ -611,7 +629,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
         }
         --count;
         ++n_iter;
-        ops += a.stack_cost;
+        ops += stack_cost;
         const int p_sched = int(p_meta >> 16);
         const uint32_t p_snap = p_aux & 0xFFu;
         const uint32_t p_mask = (p_aux >> 8) & 0x1Fu;
@@ -619,7 +637,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
             status = POLAR_TIMEOUT;
             break;
         }
-        if (p_sched > a.nops) {
+        if (p_sched > c.nops) {
             status = POLAR_TIMEOUT;
             break;
         }
@@ -662,12 +680,12 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
         }
         PT(PH_BETA)
 
-        if (p_sched == a.nops) {  // a complete path
+        if (p_sched == c.nops) {  // a complete path
             if (switched) valid_lo = n;  // beta replaced, alpha left as it was
             bool pass = true;
-            if (a.crc) {
-                ops += uint32_t(a.crc) * uint32_t(W);
-                pass = crc_ok(a, w.beta, lane);
+            if (c.crc) {
+                ops += uint32_t(c.crc) * uint32_t(W);
+                pass = crc_ok(c, w.beta, lane);
             }
             if (pass) {
                 status = POLAR_OK;
@@ -683,7 +701,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
                 for (int k = lane; k < W; k += 32) sp[k] = w.beta[k];
                 __syncwarp();
             }
-            if (crc_fails >= a.L) {
+            if (crc_fails >= L) {
                 status = POLAR_CRC_FAIL;
                 out_pm = first_pm;
                 out_src = 2;
@@ -697,7 +715,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
         // channel, except the top stages the popped path shares with the
         // spine held now (same node, identical beta before the node) ----
         if (switched) {
-            const uint32_t tgt = __ldg(&a.ops[p_sched].z);
+            const uint32_t tgt = __ldg(&c.ops[p_sched].z);
             if (tgt != NO_TARGET) {
                 const int lam_d = int(tgt & 0xFFu);
                 const int s_d = int(tgt >> 8);
@@ -717,11 +735,11 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
         // ---- walk the schedule to the next branching node ----
         float pm = __uint_as_float(p_pmb);
         int t = p_sched;
-        const uint4 *opsv = reinterpret_cast<const uint4 *>(a.ops);
-        uint4 nxt = __ldg(opsv + min(t, a.nops - 1));
-        for (; t < a.nops; ++t) {
+        const uint4 *opsv = reinterpret_cast<const uint4 *>(c.ops);
+        uint4 nxt = __ldg(opsv + min(t, c.nops - 1));
+        for (; t < c.nops; ++t) {
             const uint4 op = nxt;
-            if (t + 1 < a.nops) nxt = __ldg(opsv + t + 1);
+            if (t + 1 < c.nops) nxt = __ldg(opsv + t + 1);
             const uint32_t code = op.x & 0xFFu;
             const int lam = int((op.x >> 8) & 0xFFu);
             const int s = int(op.y);
@@ -747,7 +765,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
             }
         }
         ++n_exp;
-        if (t == a.nops) {  // the path is complete: push it
+        if (t == c.nops) {  // the path is complete: push it
             const int slot = alloc_snapshot(st, D);
             if (slot < 0) break;
             write_snapshot(w, W, SW, slot, N, 0u, 0u, 0, 0);
@@ -757,9 +775,9 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
             cur_lo = valid_lo = n;
             clam = n;
             cs = 0;
-            ops += 1u + a.stack_cost;
+            ops += 1u + stack_cost;
             Cands one{1, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
-            insert_cands(st, count, one, pm, uint32_t(N) | (uint32_t(a.nops) << 16), seq_next, uint32_t(slot), D, lane);
+            insert_cands(st, count, one, pm, uint32_t(N) | (uint32_t(c.nops) << 16), seq_next, uint32_t(slot), D, lane);
             seq_next += 1u;
             PT(PH_DONE)
             continue;
@@ -771,12 +789,12 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
         const int lam = int((op.x >> 8) & 0xFFu);
         const int s = int(op.y);
         const int len = 1 << lam;
-        uint32_t c = 0;
-        if (lane == 0) c = ++w.cnt[op.w];
-        c = __shfl_sync(FULL, c, 0);
+        uint32_t vc = 0;
+        if (lane == 0) vc = ++w.cnt[op.w];
+        vc = __shfl_sync(FULL, vc, 0);
         __syncwarp();
-        if (int(c) >= a.L) {
-            ops += a.stack_cost;
+        if (int(vc) >= L) {
+            ops += stack_cost;
             int removed = 0;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -846,7 +864,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
         clam = lam;
         cur_lo = valid_lo = lam;
         PT(PH_SNAP)
-        ops += uint32_t(cd.nc) * a.stack_cost;
+        ops += uint32_t(cd.nc) * stack_cost;
         insert_cands(st, count, cd, pm, uint32_t(s + len) | (uint32_t(t + 1) << 16), seq_next, uint32_t(slot), D, lane);
         seq_next += uint32_t(cd.nc);
         PT(PH_INSERT)
@@ -861,7 +879,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
     }
     __syncwarp();
     ops += uint32_t(n) * uint32_t(W);
-    write_output(a, w.beta, b, lane);
+    write_output(c, w.beta, orow, lane);
     if (lane == 0) {
         if (status == POLAR_TIMEOUT) out_pm = __int_as_float(0x7f800000);
         a.pm_out[b] = out_pm;
@@ -879,81 +897,128 @@ __device__ __forceinline__ void decode_frame(const Args &a, Warp &w, unsigned b)
     PT_FLUSH
 }
 
+// One warp per frame, persistent: warps claim `chunk` frames at a time.
+// MIXED = false: every frame uses a.code, a.D, a.L and row b of the LLR and
+// message buffers.  MIXED = true: frame b has its own code, D and L
+// (a.frames[b]) and offsets into packed LLR and message buffers.
+template <bool MIXED>
 __global__ void __launch_bounds__(128) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Code codes_s[MIXED ? kMaxCodes : 1];
+    if (MIXED) {
+        for (int i = threadIdx.x; i < a.ncodes; i += blockDim.x) codes_s[i] = a.codes[i];
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     unsigned char *my = smem + size_t(wib) * a.warp_smem;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
-    Warp w{a, lane, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * a.N),
-           my + 4 * a.N + 4 * a.W, a.scratch + size_t(gwarp) * size_t(a.D + 1) * size_t(a.snap_words), nullptr};
+    uint32_t *scr = a.scratch + size_t(gwarp) * size_t(a.scratch_stride);
     for (;;) {
-        unsigned b = 0;
-        if (lane == 0) b = atomicAdd(a.counter, 1u);
-        b = __shfl_sync(FULL, b, 0);
-        if (b >= unsigned(a.B)) break;
-        w.root = a.llr + size_t(b) * a.N;
-        decode_frame(a, w, b);
+        unsigned b0 = 0;
+        if (lane == 0) b0 = atomicAdd(a.counter, unsigned(a.chunk));
+        b0 = __shfl_sync(FULL, b0, 0);
+        if (b0 >= unsigned(a.B)) break;
+        const unsigned b1 = min(unsigned(a.B), b0 + unsigned(a.chunk));
+        for (unsigned b = b0; b < b1; ++b) {
+            if (!MIXED) {
+                const Code &c = a.code;
+                Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
+                       my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N};
+                decode_frame(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
+            } else {
+                const int4 fd = a.frames[b];
+                if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
+                    if (lane == 0) {  // invalid descriptor: nothing is read or written but the status
+                        a.pm_out[b] = __int_as_float(0x7f800000);
+                        a.status_out[b] = int8_t(kBadFrame);
+                    }
+                    continue;
+                }
+                const Code &c = codes_s[fd.x];
+                const long long lo = a.llr_off[b];
+                Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
+                       reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo};
+                decode_frame(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
+            }
+        }
     }
 }
 
 }  // namespace
 
-int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *d_llr, int B, int D, int L,
-                      uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream) {
-    if (B == 0) return 0;
-    Args a{};
-    a.llr = d_llr;
-    a.B = B;
-    a.N = p->N;
-    a.n = p->n;
-    a.W = p->W;
-    a.Kmsg = p->Kmsg;
-    a.crc = p->crc;
-    a.D = D;
-    a.L = L;
-    a.ops = dt->ops;
-    a.nops = int(p->ops.size());
-    a.nbranch = p->nbranch;
-    a.crc_rows = dt->crc_rows;
-    a.msg_pos = dt->msg_pos;
-    a.info_out = d_info;
-    a.info_words = (p->Kmsg + 31) / 32;
-    a.pm_out = d_pm;
-    a.status_out = d_status;
-    a.stats_out = d_stats;
-    a.snap_words = ((p->W + 4) + 7) & ~7;
-    a.max_iter = L * (p->nbranch + 9) + 2;
-    int lg = 0;
-    while ((1 << lg) < D) ++lg;
-    a.stack_cost = 2u * uint32_t(lg < 1 ? 1 : lg);
-    a.warp_smem = ((4 * p->N + 4 * p->W + p->nbranch) + 15) & ~15;
-    a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
+Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, const uint16_t *msg_pos) {
+    Code c{};
+    c.ops = ops;
+    c.crc_rows = crc_rows;
+    c.msg_pos = msg_pos;
+    c.N = p->N;
+    c.n = p->n;
+    c.W = p->W;
+    c.Kmsg = p->Kmsg;
+    c.crc = p->crc;
+    c.nops = int(p->ops.size());
+    c.nbranch = p->nbranch;
+    c.info_words = (p->Kmsg + 31) / 32;
+    c.snap_words = ((p->W + 4) + 7) & ~7;
+    return c;
+}
 
-    int dev = 0, sms = 0;
+int warp_smem_bytes(int N, int W, int nbranch) { return ((4 * N + 4 * W + nbranch) + 15) & ~15; }
+
+// block size and persistent grid for a kernel with `warp_smem` bytes per warp
+template <bool MIXED>
+int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int *smem_out) {
+    int dev = 0, sms = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
-    int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int wpb = 4;
-    while (wpb > 1 && wpb * a.warp_smem > max_smem) wpb >>= 1;
-    if (wpb * a.warp_smem > max_smem) return POLAR_ELIMIT;
-    const int smem = wpb * a.warp_smem;
-    e = cudaFuncSetAttribute(scs_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int static_smem = MIXED ? int(sizeof(Code)) * kMaxCodes : int(sizeof(Code));
+    while (wpb > 1 && wpb * warp_smem + static_smem > max_smem) wpb >>= 1;
+    if (wpb * warp_smem + static_smem > max_smem) return POLAR_ELIMIT;
+    const int smem = wpb * warp_smem;
+    e = cudaFuncSetAttribute(scs_decode_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel<MIXED>, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return POLAR_ELIMIT;
-    long long want = (long long)(B + wpb - 1) / wpb;
     long long grid = (long long)sms * per_sm;
+    const long long want = (long long)(B + wpb - 1) / wpb;
     if (want < grid) grid = want;
+    *grid_out = int(grid);
+    *wpb_out = wpb;
+    *smem_out = smem;
+    return 0;
+}
 
-    const size_t warps = size_t(grid) * size_t(wpb);
-    const size_t scratch_words = warps * size_t(D + 1) * size_t(a.snap_words);
-    const size_t bytes = 64 + scratch_words * 4;
+int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *d_llr, int B, int D, int L,
+                      uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream) {
+    if (B == 0) return 0;
+    Args a{};
+    a.code = make_code(p, dt->ops, dt->crc_rows, dt->msg_pos);
+    a.D = D;
+    a.L = L;
+    a.llr = d_llr;
+    a.B = B;
+    a.info_out = d_info;
+    a.pm_out = d_pm;
+    a.status_out = d_status;
+    a.stats_out = d_stats;
+    a.warp_smem = warp_smem_bytes(p->N, p->W, p->nbranch);
+    a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
+    a.chunk = 1;
+    a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
+
+    int grid = 0, wpb = 0, smem = 0;
+    int rc = launch_shape<false>(a.warp_smem, B, 4, &grid, &wpb, &smem);
+    if (rc) return rc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    const size_t bytes = 64 + size_t(grid) * size_t(wpb) * size_t(a.scratch_stride) * 4;
     void *ws = nullptr;
     keep_pool_memory(dev);
     e = cudaMallocAsync(&ws, bytes, stream);
@@ -962,7 +1027,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
     e = cudaMemsetAsync(ws, 0, 64, stream);
     if (e == cudaSuccess) {
-        scs_decode_kernel<<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        scs_decode_kernel<false><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(ws, stream);
@@ -971,6 +1036,108 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed batches: frames of different codes, D and L in one persistent launch
+// ---------------------------------------------------------------------------
+
+// device table of the set's codes, made on first use (needs each plan's
+// device tables); the caller holds set->mu
+static int set_device_codes(const polar_plan_set *set, const Code **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (set->device == dev && set->d_codes) {
+        *out = static_cast<const Code *>(set->d_codes);
+        return 0;
+    }
+    if (set->device >= 0) return POLAR_EINVAL;  // a set serves one device
+    std::vector<Code> codes(set->plans.size());
+    for (size_t i = 0; i < set->plans.size(); ++i) {
+        const DeviceTables *dt = nullptr;
+        int rc = plan_device(set->plans[i], &dt);
+        if (rc) return rc;
+        codes[i] = make_code(set->plans[i], dt->ops, dt->crc_rows, dt->msg_pos);
+    }
+    void *d = nullptr;
+    e = cudaMalloc(&d, codes.size() * sizeof(Code));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemcpy(d, codes.data(), codes.size() * sizeof(Code), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_status(e);
+    }
+    set->d_codes = d;
+    set->device = dev;
+    *out = static_cast<const Code *>(d);
+    return 0;
+}
+
+void free_set_device(polar_plan_set *set) {
+    if (set->d_codes) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        cudaSetDevice(set->device);
+        cudaFree(set->d_codes);
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    set->d_codes = nullptr;
+    set->device = -1;
+}
+
+int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, int B, int Dmax, const float *d_llr,
+                            const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off, float *d_pm,
+                            int8_t *d_status, uint32_t *d_stats, cudaStream_t stream, int wpb_req, int chunk_req) {
+    if (B == 0) return 0;
+    const Code *codes = nullptr;
+    int wpb_pref, chunk;
+    {
+        std::lock_guard<std::mutex> g(set->mu);
+        int rc = set_device_codes(set, &codes);
+        if (rc) return rc;
+        wpb_pref = wpb_req > 0 ? wpb_req : (set->tuned_wpb > 0 ? set->tuned_wpb : 4);
+        chunk = chunk_req > 0 ? chunk_req : (set->tuned_chunk > 0 ? set->tuned_chunk : 1);
+    }
+    Args a{};
+    a.codes = codes;
+    a.ncodes = int(set->plans.size());
+    a.frames = d_frames;
+    a.llr_off = d_llr_off;
+    a.info_off = d_info_off;
+    a.Dmax = Dmax;
+    a.llr = d_llr;
+    a.B = B;
+    a.info_out = d_info;
+    a.pm_out = d_pm;
+    a.status_out = d_status;
+    a.stats_out = d_stats;
+    a.warp_smem = warp_smem_bytes(set->Nmax, set->Wmax, set->nbranch_max);
+    a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
+    a.chunk = chunk;
+    a.scratch_stride = (long long)(Dmax + 1) * (((set->Wmax + 4) + 7) & ~7);
+
+    int grid = 0, wpb = 0, smem = 0;
+    int rc = launch_shape<true>(a.warp_smem, (B + chunk - 1) / chunk, wpb_pref, &grid, &wpb, &smem);
+    if (rc) return rc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    const size_t bytes = 64 + size_t(grid) * size_t(wpb) * size_t(a.scratch_stride) * 4;
+    void *ws = nullptr;
+    keep_pool_memory(dev);
+    e = cudaMallocAsync(&ws, bytes, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    a.counter = reinterpret_cast<unsigned *>(ws);
+    a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
+    e = cudaMemsetAsync(ws, 0, 64, stream);
+    if (e == cudaSuccess) {
+        scs_decode_kernel<true><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(ws, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (e2 != cudaSuccess) return cuda_status(e2);
+    return 0;
+}
 
 // ---------------------------------------------------------------------------
 // Decoding without any allocation by the library.
@@ -1028,7 +1195,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
                               float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream) {
     if (B == 0) return 0;
-    int dev = 0, sms = 0, max_smem = 0;
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     StaticAreas areas;
@@ -1045,56 +1212,33 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     unsigned char *tab = static_cast<unsigned char *>(areas.tables);
 
     Args a{};
-    a.llr = d_llr;
-    a.B = B;
-    a.N = p->N;
-    a.n = p->n;
-    a.W = p->W;
-    a.Kmsg = p->Kmsg;
-    a.crc = p->crc;
+    a.code = make_code(p, reinterpret_cast<const KOp *>(tab), reinterpret_cast<const uint32_t *>(tab + rows_off),
+                       reinterpret_cast<const uint16_t *>(tab + pos_off));
     a.D = D;
     a.L = L;
-    a.ops = reinterpret_cast<const KOp *>(tab);
-    a.nops = int(p->ops.size());
-    a.nbranch = p->nbranch;
-    a.crc_rows = reinterpret_cast<const uint32_t *>(tab + rows_off);
-    a.msg_pos = reinterpret_cast<const uint16_t *>(tab + pos_off);
+    a.llr = d_llr;
+    a.B = B;
     a.info_out = d_info;
-    a.info_words = (p->Kmsg + 31) / 32;
     a.pm_out = d_pm;
     a.status_out = d_status;
     a.stats_out = d_stats;
-    a.snap_words = ((p->W + 4) + 7) & ~7;
-    a.max_iter = L * (p->nbranch + 9) + 2;
-    int lg = 0;
-    while ((1 << lg) < D) ++lg;
-    a.stack_cost = 2u * uint32_t(lg < 1 ? 1 : lg);
-    a.warp_smem = ((4 * p->N + 4 * p->W + p->nbranch) + 15) & ~15;
+    a.warp_smem = warp_smem_bytes(p->N, p->W, p->nbranch);
     a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
+    a.chunk = 1;
+    a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
 
     // as many resident warps as the static scratch holds (the kernel is
     // persistent and claims frames dynamically, so fewer warps only cost speed)
-    const size_t per_warp = size_t(D + 1) * size_t(a.snap_words) * 4;
+    const size_t per_warp = size_t(a.scratch_stride) * 4;
     const size_t warps_fit = (kStaticScratchBytes - 64) / per_warp;
     if (warps_fit < 1) return POLAR_ESCRATCH;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_status(e);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int wpb = 4;
-    while (wpb > 1 && (wpb * a.warp_smem > max_smem || size_t(wpb) > warps_fit)) wpb >>= 1;
-    if (wpb * a.warp_smem > max_smem) return POLAR_ELIMIT;
-    const int smem = wpb * a.warp_smem;
-    e = cudaFuncSetAttribute(scs_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel, wpb * 32, smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (per_sm < 1) return POLAR_ELIMIT;
-    long long grid = (long long)sms * per_sm;
-    const long long want = (long long)(B + wpb - 1) / wpb;
+    while (wpb > 1 && size_t(wpb) > warps_fit) wpb >>= 1;
+    int grid = 0, smem = 0;
+    rc = launch_shape<false>(a.warp_smem, B, wpb, &grid, &wpb, &smem);
+    if (rc) return rc;
     const long long fit = (long long)(warps_fit / size_t(wpb));
-    if (want < grid) grid = want;
-    if (fit < grid) grid = fit;
+    if (fit < grid) grid = int(fit);
 
     a.counter = static_cast<unsigned *>(areas.scratch);
     a.scratch = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(areas.scratch) + 64);
@@ -1107,7 +1251,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
         e = cudaMemcpyAsync(tab + pos_off, p->msg_pos.data(), pos_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    scs_decode_kernel<<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    scs_decode_kernel<false><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? 0 : cuda_status(e);
 }

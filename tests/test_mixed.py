@@ -1,0 +1,162 @@
+"""Mixed batches: frames of different codes, stack depths and visit caps in
+one persistent launch (scs_decode_mixed).  Each frame must come out exactly
+as if it had been decoded alone with its own plan, D and L."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import paper_1809_03606_gb300 as ps
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ps.load(build_if_missing=True)
+    return ps.load()
+
+
+# ------------------------------------------------------------ host-side checks
+def test_plan_set_validation(lib):
+    p = ps.Plan(64, 32, ps.polar_construct(64, 32, 0.0))
+    with pytest.raises(ps.PolarError):
+        ps.PlanSet([])
+    with pytest.raises(ps.PolarError):
+        ps.PlanSet([p] * 65)
+    big = ps.Plan(16384, 8192, ps.polar_construct(16384, 8192, 0.0))
+    with pytest.raises(ps.PolarError) as e:
+        ps.PlanSet([p, big])
+    assert e.value.rc == ps.POLAR_ELIMIT
+    s = ps.PlanSet([p, p])
+    d = C.c_void_p(256)
+    args = lambda B, Dmax, fr: (s.handle, fr, B, Dmax, d, d, d, d, d, d, None, None)
+    assert lib.scs_decode_mixed(*args(4, 65, d)) == ps.POLAR_ELIMIT
+    assert lib.scs_decode_mixed(*args(4, 0, d)) == ps.POLAR_EINVAL
+    assert lib.scs_decode_mixed(*args(4, 8, C.c_void_p(260))) == ps.POLAR_EINVAL  # frames not 16-byte aligned
+    assert lib.scs_decode_mixed(*args(0, 8, d)) == 0
+
+
+# ----------------------------------------------------------------- GPU tests
+def _mixed_problem(oracle, codes, B, seed, ebn0_lo=1.0, ebn0_hi=4.0):
+    """codes: list of (N, K, crc).  Returns plans, per-frame arrays and LLR rows."""
+    rng = np.random.default_rng(seed)
+    plans, frozens = [], []
+    for N, K, crc in codes:
+        fr = oracle.construct(N, K, 0.0)
+        frozens.append(fr)
+        plans.append(ps.Plan(N, K, fr, fast_nodes=True, crc=crc))
+    idx = rng.integers(0, len(codes), B).astype(np.int32)
+    D = rng.integers(1, 65, B).astype(np.int32)
+    L = rng.integers(1, 65, B).astype(np.int32)
+    eb = rng.uniform(ebn0_lo, ebn0_hi, B)
+    rows = [None] * B
+    msgs = [None] * B
+    for ci, (N, K, crc) in enumerate(codes):
+        sel = np.nonzero(idx == ci)[0]
+        if sel.size == 0:
+            continue
+        msg = W.message_bits(seed + 17 * ci, sel.size, K - crc)
+        cw = oracle.encode_batch(msg, N, K, frozens[ci], crc)
+        z = W.awgn_noise(seed + 17 * ci, sel.size, N)
+        sig = np.array([W.sigma_from_ebn0(e, K / N) for e in eb[sel]])
+        llr = W.bpsk_awgn_llr(cw, z, sig)
+        for j, b in enumerate(sel):
+            rows[b] = llr[j]
+            msgs[b] = msg[j]
+    return plans, frozens, idx, D, L, rows, msgs
+
+
+CODES = [(64, 32, 8), (128, 43, 8), (256, 171, 8), (512, 256, 8), (1024, 683, 8), (2048, 1024, 8), (256, 64, 8),
+         (128, 96, 0)]
+
+
+def _solo(torch, plan, rows, D, L):
+    x = torch.from_numpy(np.stack(rows).astype(np.float32)).cuda()
+    info, pm, st, stats = ps.decode(plan, x, int(D), int(L), with_stats=True)
+    return info.cpu().numpy(), pm.cpu().numpy(), st.cpu().numpy(), stats.cpu().numpy()
+
+
+@pytest.mark.gpu
+def test_mixed_equals_solo_and_oracle(lib, oracle_lib):
+    torch = pytest.importorskip("torch")
+    plans, frozens, idx, D, L, rows, msgs = _mixed_problem(oracle_lib, CODES, 3000, seed=5)
+    pset = ps.PlanSet(plans)
+    mb = ps.MixedBatch(pset, idx, D, L, rows)
+    stats = torch.empty((mb.B, 4), dtype=torch.int32, device="cuda")
+    mb.decode(pset, stats)
+    torch.cuda.synchronize()
+    pm = mb.pm.cpu().numpy()
+    st = mb.status.cpu().numpy()
+    stn = stats.cpu().numpy()
+    # every frame equals its solo decode (grouped by code, D and L)
+    groups = {}
+    for b in range(mb.B):
+        groups.setdefault((int(idx[b]), int(D[b]), int(L[b])), []).append(b)
+    for (ci, d, l), bs in groups.items():
+        info_s, pm_s, st_s, stats_s = _solo(torch, plans[ci], [rows[b] for b in bs], d, l)
+        for j, b in enumerate(bs):
+            assert np.array_equal(mb.message_words(b), info_s[j]), b
+            assert pm[b].view(np.uint32) == pm_s[j].view(np.uint32) and st[b] == st_s[j]
+            assert np.array_equal(stn[b], stats_s[j])
+    # and a sample against the oracle
+    for b in range(0, mb.B, 10):
+        N, K, crc = CODES[idx[b]]
+        st_o, m_o, pm_o, _, _ = oracle_lib.scs_decode(rows[b], N, K, frozens[idx[b]], fast=True, D=int(D[b]),
+                                                      L=int(L[b]), crc_len=crc)
+        got = ps.unpack_bits(mb.message_words(b)[None, :], K - crc)[0]
+        assert np.array_equal(got, m_o) and pm[b].view(np.uint32) == pm_o.view(np.uint32) and st[b] == st_o
+
+
+@pytest.mark.gpu
+def test_mixed_invalid_descriptors_are_isolated(lib, oracle_lib):
+    torch = pytest.importorskip("torch")
+    plans, frozens, idx, D, L, rows, msgs = _mixed_problem(oracle_lib, CODES[:4], 400, seed=6)
+    pset = ps.PlanSet(plans)
+    good = ps.MixedBatch(pset, idx, D, L, rows)
+    good.decode(pset)
+    mb = ps.MixedBatch(pset, idx, D, L, rows)
+    bad = [3, 50, 51, 200, 201]
+    mb.frames[3, 0] = 99  # plan index out of range
+    mb.frames[50, 1] = 0  # D < 1
+    mb.frames[51, 2] = 0  # L < 1
+    mb.frames[200, 0] = -1
+    mb.frames[201, 1] = mb.Dmax + 1  # D beyond the scratch sizing
+    mb.decode(pset)
+    torch.cuda.synchronize()
+    st = mb.status.cpu().numpy()
+    assert all(st[b] == 3 for b in bad)
+    keep = np.setdiff1d(np.arange(mb.B), bad)
+    assert np.array_equal(st[keep], good.status.cpu().numpy()[keep])
+    assert np.array_equal(mb.pm.cpu().numpy()[keep].view(np.uint32), good.pm.cpu().numpy()[keep].view(np.uint32))
+
+
+@pytest.mark.gpu
+def test_mixed_graph_replay_and_tuner(lib, oracle_lib):
+    torch = pytest.importorskip("torch")
+    plans, frozens, idx, D, L, rows, msgs = _mixed_problem(oracle_lib, CODES, 2000, seed=7)
+    pset = ps.PlanSet(plans)
+    mb = ps.MixedBatch(pset, idx, D, L, rows)
+    mb.decode(pset)  # first call on the device builds the set's tables
+    torch.cuda.synchronize()
+    ref = (mb.info.clone(), mb.pm.clone(), mb.status.clone())
+    wpb, chunk = mb.tune(pset)
+    assert wpb in (1, 2, 4) and chunk in (1, 4, 16)
+    torch.cuda.synchronize()
+    for r, g in zip(ref, (mb.info, mb.pm, mb.status)):
+        assert torch.equal(r, g)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        mb.decode(pset, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        mb.decode(pset)
+    for _ in range(2):
+        mb.info.zero_()
+        mb.pm.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for r, x in zip(ref, (mb.info, mb.pm, mb.status)):
+            assert torch.equal(r, x)
