@@ -186,6 +186,34 @@ int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, int B, int Dmax
                    const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
                    int8_t *d_status, void *stream, int *wpb_out, int *chunk_out);
 
+/* ---- Genie-aided SC with per-stage min-sum scales (differentiation) ----
+ * Built on Eq. minsum and Eq. llrcalc: with the transmitted bits known, every
+ * g uses the true partial sums, and the f output written at stage lambda is
+ * multiplied by scales[lambda] (lambda = 0 .. n-1).  The loss is the mean over
+ * frames and information leaves of softplus(-(1 - 2 u_i) L_i), the binary
+ * cross-entropy of the leaf LLR L_i against the transmitted bit u_i.
+ *  d_llr     device, [B, N] channel LLRs
+ *  d_u       device, [B, ceil(N/32)] packed transmitted bits u (frozen = 0)
+ *  d_scales  device, [n] stage scales
+ *  d_loss    device out, one value
+ *  d_leaf    device out or NULL, [B, N] leaf LLRs
+ *  d_grad_scales  device out, [n] d loss / d scales
+ *  d_grad_llr     device out or NULL, [B, N] d loss / d llr
+ * The reverse pass recomputes the forward tree (nothing is stored between
+ * calls).  Per-frame sums are reduced over frames in a fixed order:
+ * results are bit-reproducible.  Limits: the (n+1) x N tree must fit in
+ * shared memory (N <= 2048 in float, N <= 1024 in double), else POLAR_ELIMIT.
+ * Asynchronous on stream. */
+int gsc_loss(const polar_plan *plan, const float *d_llr, const uint32_t *d_u, int B, const float *d_scales,
+             float *d_loss, float *d_leaf, void *stream);
+int gsc_loss_grad(const polar_plan *plan, const float *d_llr, const uint32_t *d_u, int B, const float *d_scales,
+                  float *d_loss, float *d_grad_scales, float *d_grad_llr, void *stream);
+int gsc_loss_f64(const polar_plan *plan, const double *d_llr, const uint32_t *d_u, int B, const double *d_scales,
+                 double *d_loss, double *d_leaf, void *stream);
+int gsc_loss_grad_f64(const polar_plan *plan, const double *d_llr, const uint32_t *d_u, int B,
+                      const double *d_scales, double *d_loss, double *d_grad_scales, double *d_grad_llr,
+                      void *stream);
+
 /* Decode one frame held in host memory (synchronous), fast nodes on:
  * llr N floats in, info_out K - crc bytes (one bit per byte) out, *pm_out the
  * final path metric.  Returns the frame status (>= 0) or an error (< 0). */

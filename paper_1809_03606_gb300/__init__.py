@@ -27,6 +27,7 @@ EXPORTED = (
     "polar_construct", "polar_plan_create", "polar_plan_destroy", "polar_plan_schedule", "polar_encode_batch",
     "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info", "scs_decode_batch_noalloc",
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
+    "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64",
 )
 
 _lock = threading.Lock()
@@ -74,6 +75,10 @@ def load(build_if_missing: bool = False):
         lib.polar_plan_set_destroy.restype = None
         lib.scs_decode_mixed.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.scs_tune_mixed.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        for fn in (lib.gsc_loss, lib.gsc_loss_f64):
+            fn.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+        for fn in (lib.gsc_loss_grad, lib.gsc_loss_grad_f64):
+            fn.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
         _lib = lib
         return lib
 
@@ -332,6 +337,93 @@ class MixedBatch:
     def message_words(self, b: int) -> np.ndarray:
         lo = int(self.info_off_np[b])
         return self.info[lo:lo + int(self.words[b])].cpu().numpy()
+
+
+# ---------------------------------------- genie-aided SC (differentiation)
+def _gsc_fns(dtype):
+    import torch
+
+    if dtype == torch.float32:
+        return load().gsc_loss, load().gsc_loss_grad
+    if dtype == torch.float64:
+        return load().gsc_loss_f64, load().gsc_loss_grad_f64
+    raise TypeError("genie-aided SC runs in float32 or float64")
+
+
+def gsc_loss(plan: Plan, llr, u_words, scales, leaf=None, stream=None):
+    """Mean BCE of genie-aided SC leaf LLRs over information leaves (device scalar)."""
+    import torch
+
+    B = llr.shape[0]
+    loss = torch.empty((), dtype=llr.dtype, device=llr.device)
+    fn, _ = _gsc_fns(llr.dtype)
+    _check("gsc_loss", fn(plan.handle, _dev_ptr(llr, llr.dtype, "llr", (B, plan.N)),
+                          _dev_ptr(u_words, torch.int32, "u_words", (B, plan.words)), B,
+                          _dev_ptr(scales, llr.dtype, "scales"), C.c_void_p(loss.data_ptr()),
+                          None if leaf is None else _dev_ptr(leaf, llr.dtype, "leaf", (B, plan.N)), _stream_ptr(stream)))
+    return loss
+
+
+def gsc_loss_grad(plan: Plan, llr, u_words, scales, want_llr_grad: bool = False, stream=None):
+    """(loss, d loss/d scales, d loss/d llr or None), from the reverse kernel."""
+    import torch
+
+    B = llr.shape[0]
+    loss = torch.empty((), dtype=llr.dtype, device=llr.device)
+    gs = torch.empty_like(scales)
+    gl = torch.empty_like(llr) if want_llr_grad else None
+    _, fn = _gsc_fns(llr.dtype)
+    _check("gsc_loss_grad", fn(plan.handle, _dev_ptr(llr, llr.dtype, "llr", (B, plan.N)),
+                               _dev_ptr(u_words, torch.int32, "u_words", (B, plan.words)), B,
+                               _dev_ptr(scales, llr.dtype, "scales"), C.c_void_p(loss.data_ptr()),
+                               C.c_void_p(gs.data_ptr()), None if gl is None else C.c_void_p(gl.data_ptr()),
+                               _stream_ptr(stream)))
+    return loss, gs, gl
+
+
+def _make_genie_function():
+    import torch
+
+    class GenieSCLoss(torch.autograd.Function):
+        """loss = GenieSCLoss.apply(llr, scales, u_words, plan).  The forward
+        kernel computes the loss; backward runs the hand-written reverse kernel
+        (which recomputes the tree) for d loss/d scales and d loss/d llr."""
+
+        @staticmethod
+        def forward(ctx, llr, scales, u_words, plan):
+            llr_c, sc_c = llr.detach().contiguous(), scales.detach().contiguous()
+            ctx.save_for_backward(llr_c, sc_c, u_words)
+            ctx.plan = plan
+            return gsc_loss(plan, llr_c, u_words, sc_c)
+
+        @staticmethod
+        def backward(ctx, gout):
+            llr_c, sc_c, u_words = ctx.saved_tensors
+            _, gs, gl = gsc_loss_grad(ctx.plan, llr_c, u_words, sc_c, want_llr_grad=ctx.needs_input_grad[0])
+            return (None if gl is None else gl * gout), gs * gout, None, None
+
+    return GenieSCLoss
+
+
+_genie_cls = None
+
+
+def genie_sc_loss(llr, scales, u_words, plan: Plan):
+    """Differentiable genie-aided SC loss (see gsc_loss)."""
+    global _genie_cls
+    if _genie_cls is None:
+        _genie_cls = _make_genie_function()
+    return _genie_cls.apply(llr, scales, u_words, plan)
+
+
+def u_from_messages(plan: Plan, msg_bits: np.ndarray) -> np.ndarray:
+    """Packed transmitted u vectors [B, N/32] from message bits [B, K] (no CRC):
+    the information set in increasing index order, frozen positions 0."""
+    msg_bits = np.asarray(msg_bits, np.uint8)
+    B = msg_bits.shape[0]
+    u = np.zeros((B, plan.N), np.uint8)
+    u[:, plan.frozen == 0] = msg_bits
+    return pack_bits(u)
 
 
 def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, D: int, L: int, crc: int = 0):

@@ -25,6 +25,9 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, int
                             const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off, float *d_pm,
                             int8_t *d_status, uint32_t *d_stats, cudaStream_t stream, int wpb_req, int chunk_req);
 void free_set_device(polar_plan_set *set);
+template <typename T>
+int launch_gsc(const polar_plan *p, const uint8_t *d_info_mask, const T *d_llr, const uint32_t *d_u, int B,
+               const T *d_scales, T *d_loss, T *d_grad_scales, T *d_grad_llr, T *d_leaf, cudaStream_t stream);
 
 // Per-call scratch comes from the device's default stream-ordered pool.  By
 // default that pool returns memory to the driver at every synchronisation,
@@ -63,6 +66,7 @@ static void free_tables(DeviceTables &d) {
     cudaFree(d.msg_pos);
     cudaFree(d.info_pos);
     cudaFree(d.crc_contrib);
+    cudaFree(d.info_mask);
     d = DeviceTables{};
 }
 
@@ -83,6 +87,7 @@ int plan_device(const polar_plan *p, const DeviceTables **out) {
     if (e == cudaSuccess) e = upload(&d.msg_pos, p->msg_pos);
     if (e == cudaSuccess) e = upload(&d.info_pos, p->info_pos);
     if (e == cudaSuccess) e = upload(&d.crc_contrib, p->crc_contrib);
+    if (e == cudaSuccess) e = upload(&d.info_mask, p->info_mask);
     if (e != cudaSuccess) {
         free_tables(d);
         return cuda_status(e);
@@ -227,6 +232,41 @@ extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, int 
     if (wpb_out) *wpb_out = bw;
     if (chunk_out) *chunk_out = bc;
     return 0;
+}
+
+template <typename T>
+static int gsc_call(const polar_plan *p, const T *d_llr, const uint32_t *d_u, int B, const T *d_scales, T *d_loss,
+                    T *d_grad_scales, T *d_grad_llr, T *d_leaf, void *stream) {
+    if (!p || B < 1 || !d_llr || !d_u || !d_scales || !d_loss) return POLAR_EINVAL;
+    const DeviceTables *dt = nullptr;
+    int rc = plan_device(p, &dt);
+    if (rc) return rc;
+    return launch_gsc<T>(p, dt->info_mask, d_llr, d_u, B, d_scales, d_loss, d_grad_scales, d_grad_llr, d_leaf,
+                         cudaStream_t(stream));
+}
+
+extern "C" int gsc_loss(const polar_plan *p, const float *d_llr, const uint32_t *d_u, int B, const float *d_scales,
+                        float *d_loss, float *d_leaf, void *stream) {
+    return gsc_call<float>(p, d_llr, d_u, B, d_scales, d_loss, nullptr, nullptr, d_leaf, stream);
+}
+
+extern "C" int gsc_loss_grad(const polar_plan *p, const float *d_llr, const uint32_t *d_u, int B,
+                             const float *d_scales, float *d_loss, float *d_grad_scales, float *d_grad_llr,
+                             void *stream) {
+    if (!d_grad_scales) return POLAR_EINVAL;
+    return gsc_call<float>(p, d_llr, d_u, B, d_scales, d_loss, d_grad_scales, d_grad_llr, nullptr, stream);
+}
+
+extern "C" int gsc_loss_f64(const polar_plan *p, const double *d_llr, const uint32_t *d_u, int B,
+                            const double *d_scales, double *d_loss, double *d_leaf, void *stream) {
+    return gsc_call<double>(p, d_llr, d_u, B, d_scales, d_loss, nullptr, nullptr, d_leaf, stream);
+}
+
+extern "C" int gsc_loss_grad_f64(const polar_plan *p, const double *d_llr, const uint32_t *d_u, int B,
+                                 const double *d_scales, double *d_loss, double *d_grad_scales, double *d_grad_llr,
+                                 void *stream) {
+    if (!d_grad_scales) return POLAR_EINVAL;
+    return gsc_call<double>(p, d_llr, d_u, B, d_scales, d_loss, d_grad_scales, d_grad_llr, nullptr, stream);
 }
 
 extern "C" int polar_encode_batch(const polar_plan *p, const uint32_t *d_msg, int B, uint32_t *d_codeword,

@@ -1,0 +1,253 @@
+// gsc.cu - genie-aided SC soft decoding with per-stage min-sum scales, and
+// its hand-written reverse pass.
+//
+// Built on the SC recursions of the paper (Eq. minsum, Eq. llrcalc): with the
+// transmitted bits known, every g uses the true partial sums, so the alpha
+// tree of a frame is a fixed function of its channel LLRs and of the stage
+// scales s_lambda that multiply the f outputs written at stage lambda:
+//   left child  = s_lambda * f(a, b),   right child = b + (1 - 2 beta) a.
+// The loss is the mean over frames and information leaves of the binary
+// cross-entropy of the leaf LLR L_i against the transmitted bit u_i:
+//   softplus(-(1 - 2 u_i) L_i).
+//
+// GB300 mapping: one CTA per frame (persistent), the whole tree ((n+1) x N
+// values, stage lambda at offset lambda * N) in shared memory.  Stages are
+// computed layer by layer with every thread owning node pairs; the reverse
+// pass overwrites the stage values with their adjoints in place (a thread
+// reads and then writes the same two parent positions).  Per-frame sums go to
+// a [B, n+1] buffer that a second kernel reduces over frames in a fixed order,
+// so results do not depend on scheduling.  Templated on the value type:
+// float for training, double for gradient checks.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan.h"
+
+namespace polarscs {
+namespace {
+
+constexpr int kGscThreads = 256;
+
+template <typename T>
+struct GscArgs {
+    const T *llr;        // [B, N]
+    const uint32_t *u;   // [B, W] transmitted bits u (frozen positions 0)
+    const uint8_t *info; // [N] 1 = information leaf
+    const T *scales;     // [n]
+    int B, N, n, W;
+    int with_grad;       // run the reverse pass
+    T *frame_sums;       // [B, n + 1]: per-frame loss sum, then d/ds_lambda sums
+    T *grad_llr;         // [B, N] or null (unnormalised adjoint of the root)
+    T *leaf_out;         // [B, N] or null (leaf LLRs)
+};
+
+template <typename T>
+__device__ __forceinline__ T f_ms(T a, T b) {
+    const T m = fabs(a) < fabs(b) ? fabs(a) : fabs(b);
+    return ((a < T(0)) != (b < T(0))) ? -m : m;
+}
+
+template <typename T>
+__device__ __forceinline__ T softplus(T z) {
+    return z > T(0) ? z + log1p(exp(-z)) : log1p(exp(z));
+}
+
+// block-wide sum in a fixed order (warp shuffle tree, then warps in order)
+template <typename T>
+__device__ T block_sum(T v, T *red) {
+    for (int k = 16; k >= 1; k >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, k);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T s = T(0);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < int(blockDim.x >> 5); ++i) s += red[i];
+        red[32] = s;
+    }
+    __syncthreads();
+    s = red[32];
+    return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    T *tree = reinterpret_cast<T *>(gsm);                           // (n+1) * N
+    uint32_t *xs = reinterpret_cast<uint32_t *>(tree + (a.n + 1) * a.N);  // (n+1) * W partial sums
+    __shared__ T red[33];
+    const int N = a.N, n = a.n, W = a.W, half = N >> 1;
+    for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
+        const T *l = a.llr + size_t(b) * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) tree[size_t(n) * N + i] = l[i];
+        // partial sums: xs[lambda] = u after the encoder stages of distance 1 .. 2^(lambda-1)
+        for (int k = threadIdx.x; k < W; k += blockDim.x) xs[k] = a.u[size_t(b) * W + k];
+        __syncthreads();
+        for (int lam = 0; lam < n; ++lam) {
+            const uint32_t *src = xs + lam * W;
+            uint32_t *dst = xs + (lam + 1) * W;
+            const int d = 1 << lam;
+            for (int k = threadIdx.x; k < W; k += blockDim.x) {
+                uint32_t x = src[k];
+                if (d < 32) {
+                    const uint32_t M = d == 1 ? 0x55555555u : d == 2 ? 0x33333333u : d == 4 ? 0x0F0F0F0Fu
+                                     : d == 8 ? 0x00FF00FFu : 0x0000FFFFu;
+                    x ^= (x >> d) & M;
+                    if (N < 32) x &= (1u << N) - 1u;
+                } else {
+                    const int dw = d >> 5;
+                    if (!(k & dw)) x ^= src[k + dw];
+                }
+                dst[k] = x;
+            }
+            __syncthreads();
+        }
+        // forward, stage n-1 down to 0
+        for (int lam = n - 1; lam >= 0; --lam) {
+            const int len = 1 << lam;
+            const T s = a.scales[lam];
+            const T *par = tree + size_t(lam + 1) * N;
+            T *cur = tree + size_t(lam) * N;
+            const uint32_t *bx = xs + lam * W;
+            for (int i = threadIdx.x; i < half; i += blockDim.x) {
+                const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
+                const T x = par[ps + j], y = par[ps + len + j];
+                const int pos = ps + j;  // the left child's true bits
+                const uint32_t beta = (bx[pos >> 5] >> (pos & 31)) & 1u;
+                cur[ps + j] = s * f_ms(x, y);
+                cur[ps + len + j] = beta ? y - x : y + x;
+            }
+            __syncthreads();
+        }
+        // leaves: loss terms and the adjoint seeds (in place of the leaf values)
+        T loss = T(0);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const T L = tree[i];
+            if (a.leaf_out) a.leaf_out[size_t(b) * N + i] = L;
+            T adj = T(0);
+            if (a.info[i]) {
+                const T sg = ((xs[i >> 5] >> (i & 31)) & 1u) ? T(-1) : T(1);  // xs[0] = u
+                const T z = -sg * L;
+                loss += softplus(z);
+                adj = -sg / (T(1) + exp(-z));  // d softplus(z) / dL
+            }
+            if (a.with_grad) tree[i] = adj;
+        }
+        const T fl = block_sum(loss, red);
+        if (threadIdx.x == 0) a.frame_sums[size_t(b) * (n + 1)] = fl;
+        if (a.with_grad) {
+            __syncthreads();
+            for (int lam = 0; lam < n; ++lam) {
+                const int len = 1 << lam;
+                const T s = a.scales[lam];
+                T *par = tree + size_t(lam + 1) * N;
+                const T *cur = tree + size_t(lam) * N;
+                const uint32_t *bx = xs + lam * W;
+                T gs = T(0);
+                for (int i = threadIdx.x; i < half; i += blockDim.x) {
+                    const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
+                    const T x = par[ps + j], y = par[ps + len + j];
+                    const T gl = cur[ps + j], gr = cur[ps + len + j];
+                    const int pos = ps + j;
+                    const uint32_t beta = (bx[pos >> 5] >> (pos & 31)) & 1u;
+                    gs += gl * f_ms(x, y);
+                    const T sx = x < T(0) ? T(-1) : T(1), sy = y < T(0) ? T(-1) : T(1);
+                    T ax = beta ? -gr : gr, ay = gr;
+                    if (fabs(x) <= fabs(y)) ax += gl * s * sy;  // f = s * sgn(y) * x
+                    else ay += gl * s * sx;                     // f = s * sgn(x) * y
+                    par[ps + j] = ax;
+                    par[ps + len + j] = ay;
+                }
+                const T fg = block_sum(gs, red);
+                if (threadIdx.x == 0) a.frame_sums[size_t(b) * (n + 1) + 1 + lam] = fg;
+                __syncthreads();
+            }
+            if (a.grad_llr)
+                for (int i = threadIdx.x; i < N; i += blockDim.x) a.grad_llr[size_t(b) * N + i] = tree[size_t(n) * N + i];
+        }
+        __syncthreads();
+    }
+}
+
+// out[q] = norm * sum_b frame_sums[b, q] in a fixed order (double accumulators)
+template <typename T>
+__global__ void gsc_reduce_kernel(const T *frame_sums, int B, int Q, double norm, T *out) {
+    __shared__ double part[256];
+    const int q = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) acc += double(frame_sums[size_t(b) * Q + q]);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x >> 1; h >= 1; h >>= 1) {
+        if (int(threadIdx.x) < h) part[threadIdx.x] += part[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = T(part[0] * norm);
+}
+
+template <typename T>
+__global__ void scale_kernel(T *x, size_t n, double s) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        x[i] = T(double(x[i]) * s);
+}
+
+}  // namespace
+
+int gsc_smem_bytes(int N, int n, int W, int elem) { return (n + 1) * N * elem + (n + 1) * W * 4; }
+
+template <typename T>
+int launch_gsc(const polar_plan *p, const uint8_t *d_info_mask, const T *d_llr, const uint32_t *d_u, int B,
+               const T *d_scales, T *d_loss, T *d_grad_scales, T *d_grad_llr, T *d_leaf, cudaStream_t stream) {
+    const int N = p->N, n = p->n, W = p->W;
+    const int smem = gsc_smem_bytes(N, n, W, int(sizeof(T)));
+    int dev = 0, sms = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem + int(33 * sizeof(T)) > max_smem) return POLAR_ELIMIT;
+    e = cudaFuncSetAttribute(gsc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gsc_kernel<T>, kGscThreads, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) return POLAR_ELIMIT;
+    long long grid = (long long)sms * per_sm;
+    if (grid > B) grid = B;
+    const int Q = n + 1;
+    void *ws = nullptr;
+    keep_pool_memory(dev);
+    e = cudaMallocAsync(&ws, size_t(B) * Q * sizeof(T) + sizeof(T) * Q, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    T *sums = static_cast<T *>(ws);
+    T *red = sums + size_t(B) * Q;
+    const bool grad = d_grad_scales != nullptr || d_grad_llr != nullptr;
+    GscArgs<T> a{d_llr, d_u, d_info_mask, d_scales, B, N, n, W, grad ? 1 : 0, sums, d_grad_llr, d_leaf};
+    gsc_kernel<T><<<unsigned(grid), kGscThreads, size_t(smem), stream>>>(a);
+    e = cudaGetLastError();
+    int K = 0;
+    for (int i = 0; i < N; ++i) K += p->frozen[size_t(i)] ? 0 : 1;
+    const double norm = 1.0 / (double(B) * double(K));
+    if (e == cudaSuccess) {
+        gsc_reduce_kernel<T><<<unsigned(Q), 256, 0, stream>>>(sums, B, Q, norm, red);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && d_loss) e = cudaMemcpyAsync(d_loss, red, sizeof(T), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess && d_grad_scales)
+        e = cudaMemcpyAsync(d_grad_scales, red + 1, sizeof(T) * n, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess && d_grad_llr) {
+        scale_kernel<T><<<unsigned(sms > 0 ? sms * 4 : 64), 256, 0, stream>>>(d_grad_llr, size_t(B) * N, norm);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(ws, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return e2 == cudaSuccess ? 0 : cuda_status(e2);
+}
+
+template int launch_gsc<float>(const polar_plan *, const uint8_t *, const float *, const uint32_t *, int, const float *,
+                               float *, float *, float *, float *, cudaStream_t);
+template int launch_gsc<double>(const polar_plan *, const uint8_t *, const double *, const uint32_t *, int,
+                                const double *, double *, double *, double *, double *, cudaStream_t);
+
+}  // namespace polarscs

@@ -167,6 +167,8 @@ extern "C" int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_n
         for (int i = 0; i < N; ++i)
             if (!p->frozen[size_t(i)]) p->info_pos.push_back(uint16_t(i));
         p->msg_pos.assign(p->info_pos.begin(), p->info_pos.begin() + p->Kmsg);
+        p->info_mask.assign(size_t(N), 0u);
+        for (int i = 0; i < N; ++i) p->info_mask[size_t(i)] = p->frozen[size_t(i)] ? 0u : 1u;
 
         // CRC register of each unit message (linearity of the long division)
         if (crc) {

@@ -45,6 +45,7 @@ struct DeviceTables {
     uint16_t *msg_pos = nullptr;     // Kmsg information indices of the message bits
     uint16_t *info_pos = nullptr;    // K information indices
     uint32_t *crc_contrib = nullptr; // Kmsg CRC registers of unit messages
+    uint8_t *info_mask = nullptr;    // N bytes: 1 = information leaf
 };
 
 }  // namespace polarscs
@@ -58,6 +59,7 @@ struct polar_plan {
     std::vector<uint32_t> crc_rows;
     std::vector<uint16_t> msg_pos, info_pos;
     std::vector<uint32_t> crc_contrib;
+    std::vector<uint8_t> info_mask;
     mutable std::mutex mu;
     mutable polarscs::DeviceTables dev;
 };
