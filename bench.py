@@ -527,22 +527,25 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
     info = torch.zeros_like(m["msg"])
     pm = torch.empty(B, dtype=torch.float32, device="cuda")
     st = torch.empty(B, dtype=torch.int8, device="cuda")
+    order = torch.from_numpy(ps.polar_mixed_order(pset, fr)).cuda() if not args.no_lpt else None  # longest first
     margs = (pset, frames, Dmax, m["llr"], llr_off, info, info_off, pm, st)
-    ps.scs_decode_mixed(*margs)
+    ps.scs_decode_mixed(*margs, order=order)
     torch.cuda.synchronize()
     nsample = min(B, 200_000)
+    sfr = fr[:nsample]
+    sorder = torch.from_numpy(ps.polar_mixed_order(pset, sfr)).cuda() if not args.no_lpt else None
     sample = (pset, frames[:nsample], Dmax, m["llr"], llr_off[:nsample], info, info_off[:nsample], pm[:nsample],
               st[:nsample])
-    wpb, chunk = ps.scs_tune_mixed(*sample)
+    wpb, chunk = ps.scs_tune_mixed(*sample, order=sorder)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
-        ps.scs_decode_mixed(*margs, stream=stream)
+        ps.scs_decode_mixed(*margs, stream=stream, order=order)
     torch.cuda.current_stream().wait_stream(stream)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        ps.scs_decode_mixed(*margs)
+        ps.scs_decode_mixed(*margs, order=order)
 
     # per-configuration launches: frames grouped by (code, D), each group's
     # LLR rows gathered into its own contiguous buffer (outside the timing)
@@ -637,6 +640,7 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-frames", type=int, default=8192, help="oracle sample per point for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=1024, help="oracle sample per point per step (reference arm)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lpt", action="store_true", help="mixed workload: claim frames in batch order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -82,6 +82,14 @@ int polar_construct(int N, int K, float design_snr_db, uint8_t *frozen);
  * is needed to create or inspect a plan.  Errors: POLAR_EINVAL, POLAR_ENOMEM. */
 int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_nodes, int crc, polar_plan **out);
 
+/* Per-stage min-sum scales (not in the paper; the learnable form trained by
+ * gsc_loss_grad below): every f output written at stage lambda is multiplied
+ * by scales[lambda] (float32), lambda = 0 .. n-1.  NULL restores plain
+ * min-sum.  Host memory, n floats, copied (and pushed to the plan's device
+ * copy if it exists).  Not while a call using the plan is in flight.
+ * Errors: POLAR_EINVAL (NULL plan, non-finite scale), POLAR_ECUDA. */
+int polar_plan_set_scales(polar_plan *plan, const float *scales);
+
 /* Release a plan and its device copy (synchronous; no call using it may be
  * in flight).  NULL is ignored. */
 void polar_plan_destroy(polar_plan *plan);
@@ -161,6 +169,8 @@ void polar_plan_set_destroy(polar_plan_set *set);
 /* Decode B frames of mixed codes in one persistent launch.
  *  d_frames   device, [B, 4] int32 per frame: plan index in the set, D
  *             (1..Dmax), L (1..255), unused; 16-byte aligned
+ *  d_order    device, [B] int32 permutation of 0..B-1 giving the order in
+ *             which frames are started (e.g. polar_mixed_order), or NULL
  *  Dmax       largest D of the batch (<= 64); sizes the scratch
  *  d_llr      device float32 LLRs of all frames, packed; frame b's N values
  *             start at d_llr[d_llr_off[b]] (16-byte aligned starts are read
@@ -173,18 +183,24 @@ void polar_plan_set_destroy(polar_plan_set *set);
  * The set's device tables are made on the first call on a device (make that
  * call before any stream capture; later calls can be captured in a CUDA
  * graph).  Asynchronous on stream. */
-int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_frames, int B, int Dmax, const float *d_llr,
-                     const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
-                     int8_t *d_status, uint32_t *d_stats, void *stream);
+int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_frames, const int32_t *d_order, int B, int Dmax,
+                     const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off,
+                     float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream);
+
+/* Longest-first claim order for scs_decode_mixed (host): h_frames is the host
+ * copy of the [B, 4] descriptors, h_order receives a permutation of 0..B-1
+ * sorted by decreasing N * (8 + D).  Pass it (on the device) as d_order so
+ * that expensive frames start first.  Errors: POLAR_EINVAL. */
+int polar_mixed_order(const polar_plan_set *set, const int32_t *h_frames, int B, int32_t *h_order);
 
 /* Autotuner for scs_decode_mixed: decodes the given batch (same arguments)
  * with every combination of 1, 2 or 4 warps (frames in flight) per block and
  * 1, 4 or 16 frames claimed per atomic, times each on the stream with CUDA
  * events (synchronising), and keeps the fastest in the set for later calls.
  * *wpb_out and *chunk_out (optional) receive the choice. */
-int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, int B, int Dmax, const float *d_llr,
-                   const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
-                   int8_t *d_status, void *stream, int *wpb_out, int *chunk_out);
+int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, const int32_t *d_order, int B, int Dmax,
+                   const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off,
+                   float *d_pm, int8_t *d_status, void *stream, int *wpb_out, int *chunk_out);
 
 /* ---- Genie-aided SC with per-stage min-sum scales (differentiation) ----
  * Built on Eq. minsum and Eq. llrcalc: with the transmitted bits known, every

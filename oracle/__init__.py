@@ -58,6 +58,8 @@ def _load():
             lib.or_schedule.argtypes = [C.c_int, u8p, C.c_int, i32p, C.c_int]
             lib.or_scs_decode.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, u8p, f32p, u8p, u64p]
             lib.or_scs_decode_batch.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, u8p, f32p, i8p, u64p]
+            lib.or_scs_decode_s.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, u8p, f32p, u8p, u64p]
+            lib.or_scs_decode_batch_s.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, u8p, f32p, i8p, u64p]
             lib.or_scs_decode_exact.argtypes = [f64p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, u8p, f64p]
             lib.or_gsc_forward.argtypes = [f64p, u8p, C.c_int, f64p, f64p]
             lib.or_gsc_loss_grad.argtypes = [f64p, u8p, C.c_int, C.c_int, u8p, f64p, f64p, f64p]
@@ -124,16 +126,26 @@ def schedule(N: int, frozen: np.ndarray, fast: bool) -> list[tuple[str, int, int
     return [(OP_NAMES[int(a)], int(b), int(c)) for a, b, c in t]
 
 
-def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: bool, D: int, L: int, crc_len: int = 0):
-    """One frame.  Returns (status, msg bits [K-crc], pm, codeword [N], stats dict)."""
+def _scales_arg(scales):
+    if scales is None:
+        return None, None
+    sc = np.ascontiguousarray(scales, dtype=np.float32)
+    return sc, _p(sc, C.c_float)
+
+
+def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: bool, D: int, L: int, crc_len: int = 0,
+               scales=None):
+    """One frame.  Returns (status, msg bits [K-crc], pm, codeword [N], stats dict).
+    ``scales`` (n floats) multiplies every f output written at stage lambda."""
     llr = np.ascontiguousarray(llr, dtype=np.float32)
     fr = _u8(frozen)
     msg = np.zeros(K - crc_len, np.uint8)
     cw = np.zeros(N, np.uint8)
     pm = C.c_float(0.0)
     st = np.zeros(5, np.uint64)
-    rc = _load().or_scs_decode(_p(llr, C.c_float), N, K, _p(fr, C.c_uint8), int(bool(fast)), D, L, crc_len,
-                               _p(msg, C.c_uint8), C.byref(pm), _p(cw, C.c_uint8), _p(st, C.c_uint64))
+    sc, scp = _scales_arg(scales)
+    rc = _load().or_scs_decode_s(_p(llr, C.c_float), N, K, _p(fr, C.c_uint8), int(bool(fast)), D, L, crc_len, scp,
+                                 _p(msg, C.c_uint8), C.byref(pm), _p(cw, C.c_uint8), _p(st, C.c_uint64))
     if rc < 0:
         raise ValueError(f"or_scs_decode -> {rc}")
     stats = dict(iterations=int(st[0]), switches=int(st[1]), ops=int(st[2]), expansions=int(st[3]), max_visits=int(st[4]))
@@ -141,7 +153,7 @@ def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: boo
 
 
 def scs_decode_batch(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: bool, D: int, L: int,
-                     crc_len: int = 0, threads: int = 1):
+                     crc_len: int = 0, threads: int = 1, scales=None):
     """B frames (rows of llr).  Returns (msg [B,K-crc] u8, pm [B] f32, status [B] i8, stats [B,4] u64).
 
     ``threads`` > 1 splits the frames into contiguous chunks decoded by host
@@ -155,13 +167,14 @@ def scs_decode_batch(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fas
     status = np.zeros(B, np.int8)
     stats = np.zeros((B, 4), np.uint64)
     lib = _load()
+    sc, scp = _scales_arg(scales)
 
     def run(lo, hi):
         if hi <= lo:
             return 0
-        return lib.or_scs_decode_batch(_p(llr[lo:hi], C.c_float), hi - lo, N, K, _p(fr, C.c_uint8), int(bool(fast)), D, L,
-                                       crc_len, _p(msg[lo:hi], C.c_uint8), _p(pm[lo:hi], C.c_float),
-                                       _p(status[lo:hi], C.c_int8), _p(stats[lo:hi], C.c_uint64))
+        return lib.or_scs_decode_batch_s(_p(llr[lo:hi], C.c_float), hi - lo, N, K, _p(fr, C.c_uint8), int(bool(fast)),
+                                         D, L, crc_len, scp, _p(msg[lo:hi], C.c_uint8), _p(pm[lo:hi], C.c_float),
+                                         _p(status[lo:hi], C.c_int8), _p(stats[lo:hi], C.c_uint64))
 
     threads = max(1, min(int(threads), B))
     if threads == 1:

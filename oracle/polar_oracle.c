@@ -49,6 +49,9 @@
  *   R14 CRC: init 0, no reflection, no final xor, MSB first over the message
  *       bits in increasing info-index order; the CRC occupies the last crc
  *       info positions.
+ * Optional scaled min-sum (not in the paper; the learnable form of the
+ * genie-aided gradient below): every f output written at stage lambda is
+ * multiplied by scales[lambda] in float32.
  */
 #include <math.h>
 #include <stdint.h>
@@ -285,6 +288,7 @@ typedef struct {
     or_op *ops;
     int nops;
     const float *llr;  /* stage n: channel LLRs */
+    const float *scales; /* NULL, or per-stage factors on the f outputs (stage of the child) */
     float *amem;       /* stages 0..n-1; stage lambda has Lambda slots (Sec. 3.1) */
     float *alpha[17];
     uint8_t *beta;     /* in-place N-entry beta array (Sec. 4, Fig. fsscsbmem) */
@@ -377,7 +381,12 @@ static void calc_alpha(or_dec *d, int lam, int phi, int count) {
     const float *ap = alpha_stage(d, lam + 1);
     float *av = d->alpha[lam];
     if ((phi & 1) == 0) {
-        for (int i = 0; i < Lam; i++) av[i] = f_op(ap[i], ap[i + Lam]);
+        if (d->scales) {
+            const float sc = d->scales[lam];
+            for (int i = 0; i < Lam; i++) av[i] = sc * f_op(ap[i], ap[i + Lam]);
+        } else {
+            for (int i = 0; i < Lam; i++) av[i] = f_op(ap[i], ap[i + Lam]);
+        }
     } else {
         const uint8_t *bu = d->beta + (phi - 1) * Lam; /* beta of u = (lambda, phi - 1) */
         for (int i = 0; i < Lam; i++) av[i] = g_op(ap[i], ap[i + Lam], bu[i]);
@@ -693,11 +702,12 @@ static int scs_run(or_dec *d, const float *llr, uint8_t *msg_out, float *pm_out,
 
 /* stats (optional, 5 entries): pops, path switches, counted ops, expansions,
  * largest number of paths that branched at one node */
-int or_scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
-                  uint8_t *msg_out, float *pm_out, uint8_t *cw_out, uint64_t *stats) {
+int or_scs_decode_s(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
+                    const float *scales, uint8_t *msg_out, float *pm_out, uint8_t *cw_out, uint64_t *stats) {
     or_dec d;
     int rc = dec_init(&d, N, K, frozen, fast, D, L, crc);
     if (rc) return rc;
+    d.scales = scales;
     float pm = 0.0f;
     rc = scs_run(&d, llr, msg_out, &pm, cw_out);
     if (pm_out) *pm_out = pm;
@@ -712,13 +722,20 @@ int or_scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int fas
     return rc;
 }
 
+int or_scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
+                  uint8_t *msg_out, float *pm_out, uint8_t *cw_out, uint64_t *stats) {
+    return or_scs_decode_s(llr, N, K, frozen, fast, D, L, crc, NULL, msg_out, pm_out, cw_out, stats);
+}
+
 /* B frames, row-major llr[B][N]; msg_out[B][K-crc]; stats_out[B][4] optional
  * (iterations, switches, counted ops, expansions) */
-int or_scs_decode_batch(const float *llr, int B, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
-                        uint8_t *msg_out, float *pm_out, int8_t *status_out, uint64_t *stats_out) {
+int or_scs_decode_batch_s(const float *llr, int B, int N, int K, const uint8_t *frozen, int fast, int D, int L,
+                          int crc, const float *scales, uint8_t *msg_out, float *pm_out, int8_t *status_out,
+                          uint64_t *stats_out) {
     or_dec d;
     int rc = dec_init(&d, N, K, frozen, fast, D, L, crc);
     if (rc) return rc;
+    d.scales = scales;
     for (int b = 0; b < B; b++) {
         float pm = 0.0f;
         int st = scs_run(&d, llr + (size_t)b * N, msg_out ? msg_out + (size_t)b * (K - crc) : NULL, &pm, NULL);
@@ -733,6 +750,11 @@ int or_scs_decode_batch(const float *llr, int B, int N, int K, const uint8_t *fr
     }
     dec_free(&d);
     return OR_OK;
+}
+
+int or_scs_decode_batch(const float *llr, int B, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
+                        uint8_t *msg_out, float *pm_out, int8_t *status_out, uint64_t *stats_out) {
+    return or_scs_decode_batch_s(llr, B, N, K, frozen, fast, D, L, crc, NULL, msg_out, pm_out, status_out, stats_out);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -27,7 +27,7 @@ EXPORTED = (
     "polar_construct", "polar_plan_create", "polar_plan_destroy", "polar_plan_schedule", "polar_encode_batch",
     "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info", "scs_decode_batch_noalloc",
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
-    "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64",
+    "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64", "polar_plan_set_scales", "polar_mixed_order",
 )
 
 _lock = threading.Lock()
@@ -64,6 +64,7 @@ def load(build_if_missing: bool = False):
         lib.polar_plan_destroy.argtypes = [vp]
         lib.polar_plan_destroy.restype = None
         lib.polar_plan_schedule.argtypes = [vp, vp, i32]
+        lib.polar_plan_set_scales.argtypes = [vp, vp]
         lib.polar_encode_batch.argtypes = [vp, vp, i32, vp, vp]
         lib.polar_encode.argtypes = [vp, i32, i32, vp, i32, vp]
         lib.scs_decode_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
@@ -73,8 +74,9 @@ def load(build_if_missing: bool = False):
         lib.polar_plan_set_create.argtypes = [vp, i32, C.POINTER(vp)]
         lib.polar_plan_set_destroy.argtypes = [vp]
         lib.polar_plan_set_destroy.restype = None
-        lib.scs_decode_mixed.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
-        lib.scs_tune_mixed.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.scs_decode_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.scs_tune_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.polar_mixed_order.argtypes = [vp, vp, i32, vp]
         for fn in (lib.gsc_loss, lib.gsc_loss_f64):
             fn.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
         for fn in (lib.gsc_loss_grad, lib.gsc_loss_grad_f64):
@@ -142,6 +144,10 @@ class Plan:
     def schedule(self) -> list[tuple[str, int, int]]:
         return polar_plan_schedule(self)
 
+    def set_scales(self, scales) -> None:
+        """Per-stage min-sum scales for decoding (None: plain min-sum)."""
+        polar_plan_set_scales(self, scales)
+
     def close(self) -> None:
         if getattr(self, "_h", None) and self._h.value:
             load().polar_plan_destroy(self._h)
@@ -160,6 +166,18 @@ def polar_plan_create(N: int, K: int, frozen: np.ndarray, fast_nodes: bool = Tru
 
 def polar_plan_destroy(plan: Plan) -> None:
     plan.close()
+
+
+def polar_plan_set_scales(plan: Plan, scales) -> None:
+    if scales is None:
+        _check("polar_plan_set_scales", load().polar_plan_set_scales(plan.handle, None))
+        plan.scales = None
+        return
+    sc = np.ascontiguousarray(scales, dtype=np.float32)
+    if sc.size != int(np.log2(plan.N)):
+        raise ValueError("one scale per stage (log2 N values)")
+    _check("polar_plan_set_scales", load().polar_plan_set_scales(plan.handle, _np_ptr(sc)))
+    plan.scales = sc.copy()
 
 
 def polar_plan_schedule(plan: Plan) -> list[tuple[str, int, int]]:
@@ -264,34 +282,44 @@ def polar_plan_set_destroy(pset: PlanSet) -> None:
     pset.close()
 
 
-def _mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status):
+def _mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status, order=None):
     import torch
 
     B = frames.shape[0]
-    return (pset.handle, _dev_ptr(frames, torch.int32, "frames", (B, 4)), B, int(Dmax),
+    return (pset.handle, _dev_ptr(frames, torch.int32, "frames", (B, 4)),
+            None if order is None else _dev_ptr(order, torch.int32, "order", (B,)), B, int(Dmax),
             _dev_ptr(llr, torch.float32, "llr"), _dev_ptr(llr_off, torch.int64, "llr_off", (B,)),
             _dev_ptr(info, torch.int32, "info"), _dev_ptr(info_off, torch.int64, "info_off", (B,)),
             _dev_ptr(pm, torch.float32, "pm", (B,)), _dev_ptr(status, torch.int8, "status", (B,)))
 
 
 def scs_decode_mixed(pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_off, pm, status, stats=None,
-                     stream=None) -> None:
+                     stream=None, order=None) -> None:
     """Decode a packed batch of frames of different codes in one launch (see polarscs.h)."""
     import torch
 
     B = frames.shape[0]
     _check("scs_decode_mixed", load().scs_decode_mixed(
-        *_mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status),
+        *_mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status, order),
         None if stats is None else _dev_ptr(stats, torch.int32, "stats", (B, 4)), _stream_ptr(stream)))
 
 
-def scs_tune_mixed(pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_off, pm, status, stream=None):
+def scs_tune_mixed(pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_off, pm, status, stream=None,
+                   order=None):
     """Run the native autotuner on this batch; returns (warps per block, frames per claim)."""
     w, c = C.c_int(0), C.c_int(0)
     _check("scs_tune_mixed", load().scs_tune_mixed(
-        *_mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status), _stream_ptr(stream),
+        *_mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status, order), _stream_ptr(stream),
         C.byref(w), C.byref(c)))
     return w.value, c.value
+
+
+def polar_mixed_order(pset: PlanSet, frames_host: np.ndarray) -> np.ndarray:
+    """Longest-first claim order (host) for a [B, 4] int32 descriptor array."""
+    fr = np.ascontiguousarray(frames_host, dtype=np.int32)
+    out = np.zeros(fr.shape[0], np.int32)
+    _check("polar_mixed_order", load().polar_mixed_order(pset.handle, _np_ptr(fr), fr.shape[0], _np_ptr(out)))
+    return out
 
 
 class MixedBatch:
@@ -314,6 +342,7 @@ class MixedBatch:
         fr[:, 2] = np.asarray(L, np.int32)
         self.Dmax = int(fr[:, 1].max()) if B else 1
         self.frames = torch.from_numpy(fr).to(device)
+        self.order = torch.from_numpy(polar_mixed_order(pset, fr)).to(device) if B else None
         if isinstance(llr_rows, np.ndarray) and llr_rows.ndim == 1:
             flat = llr_rows.astype(np.float32, copy=False)
         else:
@@ -328,11 +357,11 @@ class MixedBatch:
 
     def decode(self, pset: PlanSet, stats=None, stream=None) -> None:
         scs_decode_mixed(pset, self.frames, self.Dmax, self.llr, self.llr_off, self.info, self.info_off, self.pm,
-                         self.status, stats, stream)
+                         self.status, stats, stream, self.order)
 
     def tune(self, pset: PlanSet, stream=None):
         return scs_tune_mixed(pset, self.frames, self.Dmax, self.llr, self.llr_off, self.info, self.info_off, self.pm,
-                              self.status, stream)
+                              self.status, stream, self.order)
 
     def message_words(self, b: int) -> np.ndarray:
         lo = int(self.info_off_np[b])

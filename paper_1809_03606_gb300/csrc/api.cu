@@ -21,9 +21,10 @@ int launch_polar_encode(const polar_plan *p, const DeviceTables *dt, const uint3
                         cudaStream_t stream);
 int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
                               float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream);
-int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, int B, int Dmax, const float *d_llr,
-                            const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off, float *d_pm,
-                            int8_t *d_status, uint32_t *d_stats, cudaStream_t stream, int wpb_req, int chunk_req);
+int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, const int *d_order, int B, int Dmax,
+                            const float *d_llr, const long long *d_llr_off, uint32_t *d_info,
+                            const long long *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
+                            cudaStream_t stream, int wpb_req, int chunk_req);
 void free_set_device(polar_plan_set *set);
 template <typename T>
 int launch_gsc(const polar_plan *p, const uint8_t *d_info_mask, const T *d_llr, const uint32_t *d_u, int B,
@@ -67,6 +68,7 @@ static void free_tables(DeviceTables &d) {
     cudaFree(d.info_pos);
     cudaFree(d.crc_contrib);
     cudaFree(d.info_mask);
+    cudaFree(d.scales);
     d = DeviceTables{};
 }
 
@@ -88,6 +90,7 @@ int plan_device(const polar_plan *p, const DeviceTables **out) {
     if (e == cudaSuccess) e = upload(&d.info_pos, p->info_pos);
     if (e == cudaSuccess) e = upload(&d.crc_contrib, p->crc_contrib);
     if (e == cudaSuccess) e = upload(&d.info_mask, p->info_mask);
+    if (e == cudaSuccess) e = upload(&d.scales, p->scales);
     if (e != cudaSuccess) {
         free_tables(d);
         return cuda_status(e);
@@ -111,6 +114,32 @@ extern "C" void polar_plan_destroy(polar_plan *p) {
         if (cur >= 0) cudaSetDevice(cur);
     }
     delete p;
+}
+
+extern "C" int polar_plan_set_scales(polar_plan *p, const float *scales) {
+    if (!p) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(p->mu);
+    if (scales) {
+        for (int i = 0; i < p->n; ++i)
+            if (!(scales[i] == scales[i]) || scales[i] > 3.0e38f || scales[i] < -3.0e38f) return POLAR_EINVAL;
+        p->scales.assign(scales, scales + p->n);
+    } else {
+        p->scales.clear();
+    }
+    if (p->dev.device < 0) return 0;  // the device copy is made on first use
+    int cur = -1;
+    cudaGetDevice(&cur);
+    cudaError_t e = cudaSetDevice(p->dev.device);
+    if (e == cudaSuccess && !p->scales.empty() && !p->dev.scales)
+        e = cudaMalloc(reinterpret_cast<void **>(&p->dev.scales), sizeof(float) * size_t(p->n));
+    if (e == cudaSuccess && !p->scales.empty())
+        e = cudaMemcpy(p->dev.scales, p->scales.data(), sizeof(float) * size_t(p->n), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && p->scales.empty() && p->dev.scales) {
+        e = cudaFree(p->dev.scales);
+        p->dev.scales = nullptr;
+    }
+    if (cur >= 0) cudaSetDevice(cur);
+    return e == cudaSuccess ? 0 : cuda_status(e);
 }
 
 extern "C" int scs_decode_batch(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
@@ -170,21 +199,22 @@ static int check_mixed(const polar_plan_set *set, const int32_t *d_frames, int B
     return 0;
 }
 
-extern "C" int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_frames, int B, int Dmax,
-                                const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info,
+extern "C" int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_frames, const int32_t *d_order, int B,
+                                int Dmax, const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info,
                                 const int64_t *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
                                 void *stream) {
     int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
     if (rc || B == 0) return rc;
-    return launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), B, Dmax, d_llr,
+    return launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), d_order, B, Dmax, d_llr,
                                    reinterpret_cast<const long long *>(d_llr_off), d_info,
                                    reinterpret_cast<const long long *>(d_info_off), d_pm, d_status, d_stats,
                                    cudaStream_t(stream), 0, 0);
 }
 
-extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, int B, int Dmax, const float *d_llr,
-                              const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off, float *d_pm,
-                              int8_t *d_status, void *stream, int *wpb_out, int *chunk_out) {
+extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, const int32_t *d_order, int B, int Dmax,
+                              const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info,
+                              const int64_t *d_info_off, float *d_pm, int8_t *d_status, void *stream, int *wpb_out,
+                              int *chunk_out) {
     int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
     if (rc) return rc;
     if (B == 0) return POLAR_EINVAL;
@@ -205,7 +235,7 @@ extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, int 
             float ms = 0.0f;
             for (int rep = 0; rep < 2 && rc == 0; ++rep) {  // first run warms up, the second is timed
                 cudaEventRecord(e0, s);
-                rc = launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), B, Dmax, d_llr,
+                rc = launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), d_order, B, Dmax, d_llr,
                                              reinterpret_cast<const long long *>(d_llr_off), d_info,
                                              reinterpret_cast<const long long *>(d_info_off), d_pm, d_status, nullptr,
                                              s, kWpb[wi], kChunk[ci]);
@@ -267,6 +297,23 @@ extern "C" int gsc_loss_grad_f64(const polar_plan *p, const double *d_llr, const
                                  void *stream) {
     if (!d_grad_scales) return POLAR_EINVAL;
     return gsc_call<double>(p, d_llr, d_u, B, d_scales, d_loss, d_grad_scales, d_grad_llr, nullptr, stream);
+}
+
+// Longest-first order of a mixed batch (host): frames sorted by an estimate
+// of their decoding work, N * (8 + D), descending; ties keep frame order.
+// Heavy frames then start first and light ones fill the end of the launch.
+extern "C" int polar_mixed_order(const polar_plan_set *set, const int32_t *h_frames, int B, int32_t *h_order) {
+    if (!set || B < 0 || (B > 0 && (!h_frames || !h_order))) return POLAR_EINVAL;
+    std::vector<std::pair<long long, int>> key(static_cast<size_t>(B));
+    for (int b = 0; b < B; ++b) {
+        const int pi = h_frames[4 * size_t(b)], D = h_frames[4 * size_t(b) + 1];
+        long long w = 0;
+        if (pi >= 0 && pi < int(set->plans.size())) w = (long long)set->plans[size_t(pi)]->N * (8 + std::max(D, 0));
+        key[size_t(b)] = {-w, b};
+    }
+    std::stable_sort(key.begin(), key.end());
+    for (int b = 0; b < B; ++b) h_order[b] = key[size_t(b)].second;
+    return 0;
 }
 
 extern "C" int polar_encode_batch(const polar_plan *p, const uint32_t *d_msg, int B, uint32_t *d_codeword,

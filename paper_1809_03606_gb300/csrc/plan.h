@@ -46,6 +46,7 @@ struct DeviceTables {
     uint16_t *info_pos = nullptr;    // K information indices
     uint32_t *crc_contrib = nullptr; // Kmsg CRC registers of unit messages
     uint8_t *info_mask = nullptr;    // N bytes: 1 = information leaf
+    float *scales = nullptr;         // n per-stage f scales, or null (unscaled)
 };
 
 }  // namespace polarscs
@@ -60,6 +61,7 @@ struct polar_plan {
     std::vector<uint16_t> msg_pos, info_pos;
     std::vector<uint32_t> crc_contrib;
     std::vector<uint8_t> info_mask;
+    std::vector<float> scales;  // empty: unscaled min-sum
     mutable std::mutex mu;
     mutable polarscs::DeviceTables dev;
 };

@@ -51,6 +51,7 @@ struct Code {
     const KOp *ops;
     const uint32_t *crc_rows;
     const uint16_t *msg_pos;
+    const float *scales;  // per-stage factors on f outputs, or null
     int N, n, W, Kmsg, crc, nops, nbranch, info_words;
     int snap_words;  // words per snapshot slot: W beta words + 4 meta words, padded
 };
@@ -64,6 +65,7 @@ struct Args {
     const Code *codes;          // mixed batch: frame b uses codes[frames[b].x]
     int ncodes;
     const int4 *frames;         // mixed: (code index, D, L, unused) per frame
+    const int *order;           // mixed: claim k decodes frame order[k] (null: k)
     const long long *llr_off;   // mixed: index of frame b's first LLR
     const long long *info_off;  // mixed: index of frame b's first message word
     int Dmax;                   // mixed: largest D the scratch was sized for
@@ -126,24 +128,28 @@ struct Warp {
     uint8_t *cnt;     // shared: visit counters
     uint32_t *scr;    // global: (D + 1) snapshot slots
     const float *root;
+    const float *scales;  // f output scale per stage, or null (plain min-sum)
 
     __device__ const float *stage(int lam) const { return lam == n ? root : alpha + (1 << lam); }
     __device__ bool vec_ok(int plam) const { return plam < n || llr_vec; }
 
-    // alpha of the even child (lamc) from its parent (Eq. llrcalc, f)
+    // alpha of the even child (lamc) from its parent (Eq. llrcalc, f); every
+    // f output is multiplied by the stage scale (1.0, an exact identity, for
+    // plain min-sum)
     __device__ void op_f(int lamc) const {
         const int len = 1 << lamc;
         const float *P = stage(lamc + 1);
         float *C = alpha + len;
+        const float sv = scales ? __ldg(scales + lamc) : 1.0f;
         if (len >= 128 && vec_ok(lamc + 1)) {
             for (int i = 4 * lane; i < len; i += 128) {
                 const float4 x = *reinterpret_cast<const float4 *>(P + i);
                 const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
                 float4 r;
-                r.x = f_minsum(x.x, y.x);
-                r.y = f_minsum(x.y, y.y);
-                r.z = f_minsum(x.z, y.z);
-                r.w = f_minsum(x.w, y.w);
+                r.x = __fmul_rn(sv, f_minsum(x.x, y.x));
+                r.y = __fmul_rn(sv, f_minsum(x.y, y.y));
+                r.z = __fmul_rn(sv, f_minsum(x.z, y.z));
+                r.w = __fmul_rn(sv, f_minsum(x.w, y.w));
                 *reinterpret_cast<float4 *>(C + i) = r;
             }
         } else if (len >= 64 && vec_ok(lamc + 1)) {
@@ -151,12 +157,12 @@ struct Warp {
                 const float2 x = *reinterpret_cast<const float2 *>(P + i);
                 const float2 y = *reinterpret_cast<const float2 *>(P + i + len);
                 float2 r;
-                r.x = f_minsum(x.x, y.x);
-                r.y = f_minsum(x.y, y.y);
+                r.x = __fmul_rn(sv, f_minsum(x.x, y.x));
+                r.y = __fmul_rn(sv, f_minsum(x.y, y.y));
                 *reinterpret_cast<float2 *>(C + i) = r;
             }
         } else {
-            for (int i = lane; i < len; i += 32) C[i] = f_minsum(P[i], P[i + len]);
+            for (int i = lane; i < len; i += 32) C[i] = __fmul_rn(sv, f_minsum(P[i], P[i + len]));
         }
         __syncwarp();
     }
@@ -902,7 +908,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
 // message buffers.  MIXED = true: frame b has its own code, D and L
 // (a.frames[b]) and offsets into packed LLR and message buffers.
 template <bool MIXED>
-__global__ void __launch_bounds__(128) scs_decode_kernel(Args a) {
+__global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Code codes_s[MIXED ? kMaxCodes : 1];
     if (MIXED) {
@@ -920,11 +926,13 @@ __global__ void __launch_bounds__(128) scs_decode_kernel(Args a) {
         b0 = __shfl_sync(FULL, b0, 0);
         if (b0 >= unsigned(a.B)) break;
         const unsigned b1 = min(unsigned(a.B), b0 + unsigned(a.chunk));
-        for (unsigned b = b0; b < b1; ++b) {
+        for (unsigned k = b0; k < b1; ++k) {
+            const unsigned b = (MIXED && a.order) ? unsigned(__ldg(a.order + k)) : k;
+            if (MIXED && b >= unsigned(a.B)) continue;
             if (!MIXED) {
                 const Code &c = a.code;
                 Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
-                       my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N};
+                       my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
                 decode_frame(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
             } else {
                 const int4 fd = a.frames[b];
@@ -938,7 +946,7 @@ __global__ void __launch_bounds__(128) scs_decode_kernel(Args a) {
                 const Code &c = codes_s[fd.x];
                 const long long lo = a.llr_off[b];
                 Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
-                       reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo};
+                       reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales};
                 decode_frame(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
             }
         }
@@ -947,9 +955,11 @@ __global__ void __launch_bounds__(128) scs_decode_kernel(Args a) {
 
 }  // namespace
 
-Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, const uint16_t *msg_pos) {
+Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, const uint16_t *msg_pos,
+               const float *scales) {
     Code c{};
     c.ops = ops;
+    c.scales = p->scales.empty() ? nullptr : scales;
     c.crc_rows = crc_rows;
     c.msg_pos = msg_pos;
     c.N = p->N;
@@ -998,7 +1008,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
                       uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats, cudaStream_t stream) {
     if (B == 0) return 0;
     Args a{};
-    a.code = make_code(p, dt->ops, dt->crc_rows, dt->msg_pos);
+    a.code = make_code(p, dt->ops, dt->crc_rows, dt->msg_pos, dt->scales);
     a.D = D;
     a.L = L;
     a.llr = d_llr;
@@ -1056,7 +1066,7 @@ static int set_device_codes(const polar_plan_set *set, const Code **out) {
         const DeviceTables *dt = nullptr;
         int rc = plan_device(set->plans[i], &dt);
         if (rc) return rc;
-        codes[i] = make_code(set->plans[i], dt->ops, dt->crc_rows, dt->msg_pos);
+        codes[i] = make_code(set->plans[i], dt->ops, dt->crc_rows, dt->msg_pos, dt->scales);
     }
     void *d = nullptr;
     e = cudaMalloc(&d, codes.size() * sizeof(Code));
@@ -1084,9 +1094,10 @@ void free_set_device(polar_plan_set *set) {
     set->device = -1;
 }
 
-int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, int B, int Dmax, const float *d_llr,
-                            const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off, float *d_pm,
-                            int8_t *d_status, uint32_t *d_stats, cudaStream_t stream, int wpb_req, int chunk_req) {
+int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, const int *d_order, int B, int Dmax,
+                            const float *d_llr, const long long *d_llr_off, uint32_t *d_info,
+                            const long long *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
+                            cudaStream_t stream, int wpb_req, int chunk_req) {
     if (B == 0) return 0;
     const Code *codes = nullptr;
     int wpb_pref, chunk;
@@ -1101,6 +1112,7 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, int
     a.codes = codes;
     a.ncodes = int(set->plans.size());
     a.frames = d_frames;
+    a.order = d_order;
     a.llr_off = d_llr_off;
     a.info_off = d_info_off;
     a.Dmax = Dmax;
@@ -1208,12 +1220,14 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     const size_t rows_bytes = p->crc_rows.size() * sizeof(uint32_t);
     const size_t pos_off = align_up(rows_off + rows_bytes, 256);
     const size_t pos_bytes = p->msg_pos.size() * sizeof(uint16_t);
-    if (pos_off + pos_bytes > kStaticTableBytes) return POLAR_ESCRATCH;
+    const size_t sc_off = align_up(pos_off + pos_bytes, 256);
+    const size_t sc_bytes = p->scales.size() * sizeof(float);
+    if (sc_off + sc_bytes > kStaticTableBytes) return POLAR_ESCRATCH;
     unsigned char *tab = static_cast<unsigned char *>(areas.tables);
 
     Args a{};
     a.code = make_code(p, reinterpret_cast<const KOp *>(tab), reinterpret_cast<const uint32_t *>(tab + rows_off),
-                       reinterpret_cast<const uint16_t *>(tab + pos_off));
+                       reinterpret_cast<const uint16_t *>(tab + pos_off), reinterpret_cast<const float *>(tab + sc_off));
     a.D = D;
     a.L = L;
     a.llr = d_llr;
@@ -1249,6 +1263,8 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
         e = cudaMemcpyAsync(tab + rows_off, p->crc_rows.data(), rows_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && pos_bytes)
         e = cudaMemcpyAsync(tab + pos_off, p->msg_pos.data(), pos_bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && sc_bytes)
+        e = cudaMemcpyAsync(tab + sc_off, p->scales.data(), sc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_status(e);
     scs_decode_kernel<false><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);

@@ -176,3 +176,28 @@ def test_streams_and_repeatability(oracle_lib):
     torch.cuda.synchronize()
     for r, g in zip(ref, again):
         assert torch.equal(r, g)
+
+
+@pytest.mark.parametrize("N,K,crc,fast,D,L", [(256, 128, 0, False, 16, 4), (1024, 512, 16, True, 32, 32)])
+def test_scaled_min_sum_parity(oracle_lib, N, K, crc, fast, D, L):
+    """Per-stage f scales (plan option) against the oracle's scaled decoder; a
+    plan whose scales are reset decodes exactly like the unscaled one."""
+    fr, msg, cw, llr = make_frames(oracle_lib, N, K, crc, 600, 2.0, seed=31)
+    n = int(np.log2(N))
+    scales = np.random.default_rng(n).uniform(0.55, 1.25, n).astype(np.float32)
+    plan = ps.Plan(N, K, fr, fast_nodes=fast, crc=crc)
+    plan.set_scales(scales)
+    x = torch.from_numpy(llr).cuda()
+    info, pm, st, stats = ps.decode(plan, x, D, L, with_stats=True)
+    torch.cuda.synchronize()
+    m_o, pm_o, st_o, stats_o = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=fast, D=D, L=L, crc_len=crc,
+                                                           threads=8, scales=scales)
+    assert np.array_equal(ps.unpack_bits(info.cpu().numpy(), K - crc), m_o)
+    assert np.array_equal(pm.cpu().numpy().view(np.uint32), pm_o.view(np.uint32))
+    assert np.array_equal(st.cpu().numpy(), st_o)
+    plan.set_scales(None)
+    info2, pm2, st2 = ps.decode(plan, x, D, L)
+    torch.cuda.synchronize()
+    m_u, pm_u, st_u, _ = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=fast, D=D, L=L, crc_len=crc, threads=8)
+    assert np.array_equal(ps.unpack_bits(info2.cpu().numpy(), K - crc), m_u)
+    assert np.array_equal(pm2.cpu().numpy().view(np.uint32), pm_u.view(np.uint32))

@@ -29,7 +29,7 @@ def test_plan_set_validation(lib):
     assert e.value.rc == ps.POLAR_ELIMIT
     s = ps.PlanSet([p, p])
     d = C.c_void_p(256)
-    args = lambda B, Dmax, fr: (s.handle, fr, B, Dmax, d, d, d, d, d, d, None, None)
+    args = lambda B, Dmax, fr: (s.handle, fr, None, B, Dmax, d, d, d, d, d, d, None, None)
     assert lib.scs_decode_mixed(*args(4, 65, d)) == ps.POLAR_ELIMIT
     assert lib.scs_decode_mixed(*args(4, 0, d)) == ps.POLAR_EINVAL
     assert lib.scs_decode_mixed(*args(4, 8, C.c_void_p(260))) == ps.POLAR_EINVAL  # frames not 16-byte aligned

@@ -184,6 +184,22 @@ def test_scs_depth1_is_sc(oracle_lib, N, K):
         assert pm == pm_sc
 
 
+@pytest.mark.parametrize("N,K", [(64, 32), (256, 128)])
+def test_scaled_scs_depth1_is_scaled_sc(oracle_lib, N, K):
+    """With per-stage scales on f, SCS(D = 1) is the scaled SC decoder, bit for
+    bit; unit scales reproduce the unscaled decoder exactly."""
+    fr, msg, cw, llr = _frames(oracle_lib, N, K, 0, 120, 1.5, seed=19)
+    n = int(np.log2(N))
+    scales = np.random.default_rng(N).uniform(0.5, 1.3, n).astype(np.float32)
+    for b in range(llr.shape[0]):
+        _, x_sc, pm_sc = tb.sc_decode(llr[b], fr, scales)
+        st, m, pm, xhat, _ = oracle_lib.scs_decode(llr[b], N, K, fr, fast=False, D=1, L=4, scales=scales)
+        assert np.array_equal(xhat, x_sc) and pm == pm_sc
+        st1, m1, pm1, x1, _ = oracle_lib.scs_decode(llr[b], N, K, fr, fast=True, D=8, L=8, scales=np.ones(n))
+        st0, m0, pm0, x0, _ = oracle_lib.scs_decode(llr[b], N, K, fr, fast=True, D=8, L=8)
+        assert np.array_equal(x1, x0) and pm1 == pm0
+
+
 @pytest.mark.parametrize("N,K,D", [(64, 32, 8), (256, 128, 16)])
 def test_scs_visit_cap_one_is_sc(oracle_lib, N, K, D):
     """L = 1 deletes every older path at each branching: again SC."""

@@ -49,11 +49,13 @@ def f_minsum(a, b):
     return np.where(np.signbit(a) ^ np.signbit(b), -m, m).astype(F32)
 
 
-def sc_decode(llr: np.ndarray, frozen: np.ndarray):
+def sc_decode(llr: np.ndarray, frozen: np.ndarray, scales=None):
     """Arikan's recursive SC decoder with min-sum f, float32 throughout.
 
     Returns (u_hat, codeword, pm) where pm accumulates |alpha| at every leaf
     whose decision differs from the hard decision of its LLR (Eq. PMupd).
+    ``scales[lambda]`` (optional) multiplies the f output of a child at stage
+    lambda.
     """
     pm = [F32(0.0)]
 
@@ -68,7 +70,10 @@ def sc_decode(llr: np.ndarray, frozen: np.ndarray):
             return np.array([u], np.uint8), np.array([u], np.uint8)
         h = n // 2
         a, b = alpha[:h], alpha[h:]
-        ul, xl = rec(f_minsum(a, b), fr[:h])
+        fv = f_minsum(a, b)
+        if scales is not None:
+            fv = (F32(scales[int(np.log2(h))]) * fv).astype(F32)
+        ul, xl = rec(fv, fr[:h])
         right = np.where(xl.astype(bool), (b - a).astype(F32), (b + a).astype(F32)).astype(F32)
         ur, xr = rec(right, fr[h:])
         return np.concatenate([ul, ur]), np.concatenate([xl ^ xr, xr])
