@@ -56,6 +56,9 @@ extern "C" {
                                exceed its 1 MiB static table area, or one
                                warp's scratch exceeds its 16 MiB static array */
 
+#define POLAR_ETIMEOUT (-6) /* polar_serve*: a bounded wait ran out (requests left
+                               undecoded; the engine stopped cleanly) */
+
 /* Maximum sizes the GPU decoder accepts. */
 #define POLAR_MAX_N_GPU 8192
 #define POLAR_MAX_D_GPU 64
@@ -229,6 +232,38 @@ int gsc_loss_f64(const polar_plan *plan, const double *d_llr, const uint32_t *d_
 int gsc_loss_grad_f64(const polar_plan *plan, const double *d_llr, const uint32_t *d_u, int B,
                       const double *d_scales, double *d_loss, double *d_grad_scales, double *d_grad_llr,
                       void *stream);
+
+/* ---- Serving (continuous batching) ----
+ * Not a construct of the paper: a serving form of the same decoder.  Requests
+ * arrive at given times (seconds from the start of the call, non-decreasing).
+ * Request r is (plan index in the set, D, L, pool frame) = req[4r .. 4r+3];
+ * its N LLRs are pool_llr[pool_off[frame] ..] (host memory; registered for
+ * asynchronous copies during the call).
+ *  polar_serve keeps one persistent kernel resident: each warp claims the
+ *  next request, waits until the host has released it, decodes it and
+ *  raises its completion flag, so requests that arrive while others are
+ *  being decoded start as soon as a warp and arena space free up.  A request
+ *  is released once it has arrived and its LLRs fit in the device arena of
+ *  arena_floats floats (the HBM budget; space is returned when the oldest
+ *  outstanding requests complete).  Every device and host wait is bounded by
+ *  wait_s seconds; on time-out the engine stops and returns POLAR_ETIMEOUT.
+ *  polar_serve_baseline decodes one size per launch: every interval_s the
+ *  arrived requests are grouped by (plan, D, L) and each group is a separate
+ *  scs_decode_batch launch.
+ * Outputs per request: pm_out, status_out (as scs_decode_batch; 127 if never
+ * decoded), latency_out (completion - arrival, seconds; -1 if not completed)
+ * and, for polar_serve, the packed message words at info_off[r] of info_out
+ * (both may be NULL).  report (6 doubles): seconds from start to the last
+ * completion, arena-full stalls, error flag, most requests in flight (serve) or
+ * launches (baseline), requests completed, arena bytes. */
+int polar_serve(const polar_plan_set *set, const int32_t *req, const double *arrival_s, int R, const float *pool_llr,
+                const int64_t *pool_off, int P, int64_t arena_floats, double wait_s, float *pm_out,
+                int8_t *status_out, uint32_t *info_out, const int64_t *info_off, double *latency_out,
+                double *report);
+int polar_serve_baseline(const polar_plan_set *set, const int32_t *req, const double *arrival_s, int R,
+                         const float *pool_llr, const int64_t *pool_off, int P, int64_t arena_floats,
+                         double interval_s, double wait_s, float *pm_out, int8_t *status_out, double *latency_out,
+                         double *report);
 
 /* Decode one frame held in host memory (synchronous), fast nodes on:
  * llr N floats in, info_out K - crc bytes (one bit per byte) out, *pm_out the

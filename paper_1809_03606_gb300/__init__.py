@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 POLAR_OK, POLAR_CRC_FAIL, POLAR_TIMEOUT = 0, 1, 2
-POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ELIMIT, POLAR_ESCRATCH = -1, -2, -3, -4, -5
+POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ELIMIT, POLAR_ESCRATCH, POLAR_ETIMEOUT = -1, -2, -3, -4, -5, -6
 MAX_N_GPU, MAX_D_GPU, MAX_L_GPU = 8192, 64, 255
 OP_NAMES = {0: "alpha", 1: "beta", 2: "R0", 3: "R1", 4: "REP", 5: "SPC", 6: "leaf0", 7: "leaf1"}
 
@@ -28,6 +28,7 @@ EXPORTED = (
     "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info", "scs_decode_batch_noalloc",
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
     "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64", "polar_plan_set_scales", "polar_mixed_order",
+    "polar_serve", "polar_serve_baseline",
 )
 
 _lock = threading.Lock()
@@ -36,7 +37,7 @@ _lib = None
 
 class PolarError(RuntimeError):
     def __init__(self, fn: str, rc: int):
-        names = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT", -5: "ESCRATCH"}
+        names = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELIMIT", -5: "ESCRATCH", -6: "ETIMEOUT"}
         super().__init__(f"{fn} failed: {names.get(rc, rc)}")
         self.rc = rc
 
@@ -77,6 +78,9 @@ def load(build_if_missing: bool = False):
         lib.scs_decode_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.scs_tune_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.polar_mixed_order.argtypes = [vp, vp, i32, vp]
+        i64, f64 = C.c_int64, C.c_double
+        lib.polar_serve.argtypes = [vp, vp, vp, i32, vp, vp, i32, i64, f64, vp, vp, vp, vp, vp, vp]
+        lib.polar_serve_baseline.argtypes = [vp, vp, vp, i32, vp, vp, i32, i64, f64, f64, vp, vp, vp, vp]
         for fn in (lib.gsc_loss, lib.gsc_loss_f64):
             fn.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
         for fn in (lib.gsc_loss_grad, lib.gsc_loss_grad_f64):
@@ -453,6 +457,64 @@ def u_from_messages(plan: Plan, msg_bits: np.ndarray) -> np.ndarray:
     u = np.zeros((B, plan.N), np.uint8)
     u[:, plan.frozen == 0] = msg_bits
     return pack_bits(u)
+
+
+# ------------------------------------------------------------------ serving
+_REPORT = ("seconds_to_last_completion", "arena_full_stalls", "error", "max_in_flight_or_launches", "completed",
+           "arena_bytes")
+
+
+def _serve_inputs(req, arrival_s, pool_llr, pool_off):
+    req = np.ascontiguousarray(req, dtype=np.int32).reshape(-1, 4)
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    pool = np.ascontiguousarray(pool_llr, dtype=np.float32).reshape(-1)
+    poff = np.ascontiguousarray(pool_off, dtype=np.int64)
+    if arr.size != req.shape[0]:
+        raise ValueError("one arrival time per request")
+    return req, arr, pool, poff
+
+
+def polar_serve(pset: PlanSet, req, arrival_s, pool_llr, pool_off, arena_floats: int, wait_s: float = 30.0,
+                info_off=None) -> dict:
+    """Continuous-batching engine (see polarscs.h).  Returns per-request pm,
+    status, latency (s), optional message words, and the engine report."""
+    req, arr, pool, poff = _serve_inputs(req, arrival_s, pool_llr, pool_off)
+    R = req.shape[0]
+    pm = np.zeros(R, np.float32)
+    st = np.zeros(R, np.int8)
+    lat = np.zeros(R, np.float64)
+    rep = np.zeros(6, np.float64)
+    info = ioff = None
+    if info_off is not None:
+        ioff = np.ascontiguousarray(info_off, dtype=np.int64)
+        words = np.array([pset.plans[int(i)].msg_words for i in req[:, 0]], np.int64)
+        info = np.zeros(int((ioff + words).max()), np.uint32)
+    rc = load().polar_serve(pset.handle, _np_ptr(req), _np_ptr(arr), R, _np_ptr(pool), _np_ptr(poff), poff.size,
+                            int(arena_floats), float(wait_s), _np_ptr(pm), _np_ptr(st),
+                            None if info is None else _np_ptr(info), None if ioff is None else _np_ptr(ioff),
+                            _np_ptr(lat), _np_ptr(rep))
+    out = dict(rc=rc, pm=pm, status=st, latency=lat, info=info, report=dict(zip(_REPORT, rep.tolist())))
+    if rc < 0 and rc != POLAR_ETIMEOUT:
+        raise PolarError("polar_serve", rc)
+    return out
+
+
+def polar_serve_baseline(pset: PlanSet, req, arrival_s, pool_llr, pool_off, arena_floats: int,
+                         interval_s: float = 1e-3, wait_s: float = 30.0) -> dict:
+    """One-size-per-launch baseline engine over the same request stream."""
+    req, arr, pool, poff = _serve_inputs(req, arrival_s, pool_llr, pool_off)
+    R = req.shape[0]
+    pm = np.zeros(R, np.float32)
+    st = np.zeros(R, np.int8)
+    lat = np.zeros(R, np.float64)
+    rep = np.zeros(6, np.float64)
+    rc = load().polar_serve_baseline(pset.handle, _np_ptr(req), _np_ptr(arr), R, _np_ptr(pool), _np_ptr(poff),
+                                     poff.size, int(arena_floats), float(interval_s), float(wait_s), _np_ptr(pm),
+                                     _np_ptr(st), _np_ptr(lat), _np_ptr(rep))
+    out = dict(rc=rc, pm=pm, status=st, latency=lat, report=dict(zip(_REPORT, rep.tolist())))
+    if rc < 0 and rc != POLAR_ETIMEOUT:
+        raise PolarError("polar_serve_baseline", rc)
+    return out
 
 
 def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, D: int, L: int, crc: int = 0):

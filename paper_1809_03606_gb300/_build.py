@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpolarscs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "api.cu", "scs_decode.cu", "encode.cu", "gsc.cu"]
+SOURCES = ["plan.cpp", "api.cu", "scs_decode.cu", "encode.cu", "gsc.cu", "serve.cpp"]
 # -fmad=false: the decoder's float arithmetic must not be contracted (bit
 # parity with the CPU oracle); nothing in these kernels multiplies and adds.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -81,6 +81,14 @@ struct Args {
     int warp_smem;              // bytes of shared memory per warp
     int llr_vec;                // the LLR buffer is 16-byte aligned
     int chunk;                  // frames claimed per atomic
+    // served mode: requests become decodable when the host publishes them
+    const unsigned long long *head;  // device: requests [0, head) are published
+    const int *abort_flag;           // host-mapped: stop waiting
+    unsigned char *done_flag;        // host-mapped: 1 when request k is complete
+    unsigned long long *t_done;      // device: %globaltimer at completion
+    int *error_flag;                 // device: a wait ran out
+    unsigned long long wait_ns;      // longest wait for one request
+    long long serve_stage_off;       // words into a warp's scratch where its LLR staging starts
 };
 
 // Optional per-phase cycle counters (debug builds with -DPOLAR_PHASE_TIMERS):
@@ -953,6 +961,82 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Served requests (continuous batching): warps claim request indices in
+// order, wait until the host has published the request (its LLRs copied into
+// the arena), decode it as a mixed-batch frame, stamp the completion time and
+// raise its completion flag in host-mapped memory.  Every wait is bounded:
+// after wait_ns (or when the host raises abort_flag) the warp records an
+// error and leaves.  Request LLRs live in an arena the host refills once the
+// requests that used it have completed; since an SM's L1 may still hold lines
+// of an earlier request there, a warp first copies its request's LLRs with
+// L2-only loads into its own staging area (its own stores keep its L1
+// coherent) and decodes from that copy.
+__global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Code codes_s[kMaxCodes];
+    for (int i = threadIdx.x; i < a.ncodes; i += blockDim.x) codes_s[i] = a.codes[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char *my = smem + size_t(wib) * a.warp_smem;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
+    uint32_t *scr = a.scratch + size_t(gwarp) * size_t(a.scratch_stride);
+    for (;;) {
+        unsigned k = 0;
+        int ok = 1;
+        if (lane == 0) {
+            k = atomicAdd(a.counter, 1u);
+            if (k < unsigned(a.B)) {
+                const unsigned long long t0 = global_ns();
+                unsigned ns = 64;
+                while (*reinterpret_cast<const volatile unsigned long long *>(a.head) <= k) {
+                    if (*reinterpret_cast<const volatile int *>(a.abort_flag) || global_ns() - t0 > a.wait_ns) {
+                        ok = 0;
+                        atomicExch(a.error_flag, 1);
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 8192) ns <<= 1;
+                }
+                __threadfence();
+            }
+        }
+        k = __shfl_sync(FULL, k, 0);
+        ok = __shfl_sync(FULL, ok, 0);
+        if (k >= unsigned(a.B) || !ok) break;
+        const int4 fd = a.frames[k];
+        if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
+            if (lane == 0) {
+                a.pm_out[k] = __int_as_float(0x7f800000);
+                a.status_out[k] = int8_t(kBadFrame);
+            }
+        } else {
+            const Code &c = codes_s[fd.x];
+            const float *src = a.llr + a.llr_off[k];
+            float *stage = reinterpret_cast<float *>(scr + a.serve_stage_off);
+            for (int i = lane; i < c.N; i += 32) stage[i] = __ldcg(src + i);
+            __syncwarp();
+            Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
+                   my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
+            decode_frame(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
+        }
+        if (lane == 0) {
+            a.t_done[k] = global_ns();
+            __threadfence_system();
+            reinterpret_cast<volatile unsigned char *>(a.done_flag)[k] = 1;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void read_global_ns(unsigned long long *out) { *out = global_ns(); }
+
 }  // namespace
 
 Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, const uint16_t *msg_pos,
@@ -1149,6 +1233,87 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     if (e != cudaSuccess) return cuda_status(e);
     if (e2 != cudaSuccess) return cuda_status(e2);
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Served requests: the persistent kernel of the continuous-batching engine
+// ---------------------------------------------------------------------------
+int serve_codes(const polar_plan_set *set, const void **out) {
+    std::lock_guard<std::mutex> g(set->mu);
+    const Code *c = nullptr;
+    int rc = set_device_codes(set, &c);
+    *out = c;
+    return rc;
+}
+
+int launch_scs_serve(const polar_plan_set *set, const void *codes_v, const int4 *d_frames, int B, int Dmax,
+                     const float *d_arena, const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off,
+                     float *d_pm, int8_t *d_status, const unsigned long long *d_head, const int *h_abort,
+                     unsigned char *h_done, unsigned long long *d_t_done, int *d_error, unsigned long long wait_ns,
+                     unsigned *d_counter, uint32_t *d_scratch, size_t scratch_bytes, int wpb_pref,
+                     cudaStream_t stream) {
+    const Code *codes = static_cast<const Code *>(codes_v);
+    Args a{};
+    a.codes = codes;
+    a.ncodes = int(set->plans.size());
+    a.frames = d_frames;
+    a.llr_off = d_llr_off;
+    a.info_off = d_info_off;
+    a.Dmax = Dmax;
+    a.llr = d_arena;
+    a.B = B;
+    a.info_out = d_info;
+    a.pm_out = d_pm;
+    a.status_out = d_status;
+    a.warp_smem = warp_smem_bytes(set->Nmax, set->Wmax, set->nbranch_max);
+    a.llr_vec = 1;  // requests are decoded from 16-byte aligned staging copies
+    a.chunk = 1;
+    a.serve_stage_off = (long long)(Dmax + 1) * (((set->Wmax + 4) + 7) & ~7);
+    a.scratch_stride = a.serve_stage_off + ((set->Nmax + 3) & ~3);
+    a.head = d_head;
+    a.abort_flag = h_abort;
+    a.done_flag = h_done;
+    a.t_done = d_t_done;
+    a.error_flag = d_error;
+    a.wait_ns = wait_ns;
+    a.counter = d_counter;
+    a.scratch = d_scratch;
+    int dev = 0, sms = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int wpb = wpb_pref > 0 ? wpb_pref : 4;
+    const int static_smem = int(sizeof(Code)) * kMaxCodes;
+    while (wpb > 1 && wpb * a.warp_smem + static_smem > max_smem) wpb >>= 1;
+    const int smem = wpb * a.warp_smem;
+    e = cudaFuncSetAttribute(scs_serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_serve_kernel, wpb * 32, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) return POLAR_ELIMIT;
+    long long grid = (long long)sms * per_sm;
+    const size_t per_block = size_t(wpb) * size_t(a.scratch_stride) * 4;
+    if (size_t(grid) * per_block > scratch_bytes) grid = (long long)(scratch_bytes / per_block);
+    if (grid < 1) return POLAR_ENOMEM;
+    scs_serve_kernel<<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : cuda_status(e);
+}
+
+size_t serve_scratch_bytes(const polar_plan_set *set, int Dmax) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t stride = (size_t(Dmax + 1) * size_t(((set->Wmax + 4) + 7) & ~7) + size_t((set->Nmax + 3) & ~3)) * 4;
+    return size_t(sms > 0 ? sms : 1) * 8 * 4 * stride;  // at most 8 blocks of 4 warps per SM
+}
+
+int read_device_ns(unsigned long long *d_out, cudaStream_t s) {
+    read_global_ns<<<1, 1, 0, s>>>(d_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : cuda_status(e);
 }
 
 // ---------------------------------------------------------------------------
