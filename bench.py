@@ -615,6 +615,82 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ served workload
+SERVE = dict(rate=5e6, seconds=10.0, pool=1 << 18, seed=5, arena_bytes=2 << 30, interval_s=2e-3, compare_seconds=0.5)
+
+
+def bench_serve(args, rank: int, world: int, local_rank: int) -> None:
+    """Poisson arrivals drawn from the mixed workload's code/D/Eb-N0 mix,
+    served by the continuous-batching engine and by the one-size-per-launch
+    baseline on the same request stream; p50/p99 latency and throughput."""
+    import numpy as np
+    import torch
+
+    import paper_1809_03606_gb300 as ps
+    import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    ps.load(build_if_missing=True)
+    rate = float(args.serve_rate or SERVE["rate"])
+    seconds = float(args.serve_seconds or SERVE["seconds"])
+    m = make_mixed_inputs(ps, SERVE["pool"], rank, dict(MIXED, seed=SERVE["seed"]))
+    pool = m["llr"].cpu().numpy()
+    pool_off = m["llr_off"]
+    pset = ps.PlanSet(m["plans"])
+    P = SERVE["pool"]
+    kmsg_pool = (m["Ks"] - MIXED["crc"]).astype(np.int64)
+
+    def stream(rate_hz, dur, seed):
+        arr = W.poisson_arrivals(seed, rate_hz, dur)
+        R = arr.size
+        p = np.arange(R) % P
+        req = np.stack([m["idx"][p], m["D"][p], m["D"][p], p], axis=1).astype(np.int32)
+        return req, arr, p
+
+    def summarize(out, arr, p):
+        lat = out["latency"]
+        ok = lat >= 0
+        t_end = out["report"]["seconds_to_last_completion"]
+        R = arr.size
+        bits = float(kmsg_pool[p[ok]].sum())
+        return {"requests": int(R), "completed": int(ok.sum()), "seconds": t_end,
+                "throughput_req_s": float(ok.sum()) / t_end if t_end > 0 else None,
+                "info_gbps": bits / t_end / 1e9 if t_end > 0 else None,
+                "p50_ms": float(np.percentile(lat[ok], 50) * 1e3) if ok.any() else None,
+                "p99_ms": float(np.percentile(lat[ok], 99) * 1e3) if ok.any() else None,
+                "report": out["report"]}
+
+    arena = SERVE["arena_bytes"] // 4
+    wait = max(60.0, 4 * seconds)
+    # below saturation: a short sweep
+    sweep = []
+    for r_hz in (2e5, 5e5, 1e6, 1.5e6):
+        req, arr, p = stream(r_hz, min(2.0, seconds), SERVE["seed"] + int(r_hz))
+        out = ps.polar_serve(pset, req, arr, pool, pool_off, arena, wait_s=wait)
+        sweep.append(dict(offered_req_s=r_hz, **{k: v for k, v in summarize(out, arr, p).items() if k != "report"}))
+    # the configured load served in full; both engines on the same prefix of it
+    req, arr, p = stream(rate, seconds, SERVE["seed"])
+    served = ps.polar_serve(pset, req, arr, pool, pool_off, arena, wait_s=wait)
+    s_sum = summarize(served, arr, p)
+    cut = int(np.searchsorted(arr, SERVE["compare_seconds"]))
+    sp = ps.polar_serve(pset, req[:cut], arr[:cut], pool, pool_off, arena, wait_s=wait)
+    bp = ps.polar_serve_baseline(pset, req[:cut], arr[:cut], pool, pool_off, arena, interval_s=SERVE["interval_s"],
+                                 wait_s=20 * wait)
+    same = bool(np.array_equal(sp["pm"].view(np.uint32), bp["pm"].view(np.uint32)) and
+                np.array_equal(sp["status"], bp["status"]))
+    sp_sum, b_sum = summarize(sp, arr[:cut], p[:cut]), summarize(bp, arr[:cut], p[:cut])
+    if rank == 0:
+        line = {"metric": "served decode: info Gbit/s with p50/p99 request latency", "value": s_sum["info_gbps"],
+                "unit": "Gbit/s", "n_gpus": world, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"Poisson arrivals {rate:.3g} requests/s for {seconds:g} s, each request a "
+                                       f"frame of the mixed-batch mix (pool of {P} frames cycled)",
+                           "arena_bytes": SERVE["arena_bytes"], "served": s_sum,
+                           "compare_prefix_seconds": SERVE["compare_seconds"], "served_prefix": sp_sum,
+                           "one_size_per_launch_prefix": dict(b_sum, interval_s=SERVE["interval_s"]),
+                           "identical_outputs": same, "load_sweep": sweep}}
+        print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(frames: int):
     import os as _os
 
@@ -634,8 +710,11 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "mixed"], default="sweep",
-                    help="sweep: the PC(1024,512) Eb/N0 sweep (default); mixed: the 2M-frame mixed batch")
+    ap.add_argument("--workload", choices=["sweep", "mixed", "serve"], default="sweep",
+                    help="sweep: the PC(1024,512) Eb/N0 sweep (default); mixed: the 2M-frame mixed batch; "
+                         "serve: Poisson-arrival serving")
+    ap.add_argument("--serve-rate", type=float, default=0.0, help="serve workload: arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=0.0, help="serve workload: seconds of arrivals")
     ap.add_argument("--frames", type=int, default=0, help="frames per Eb/N0 point (default 1048576)")
     ap.add_argument("--cpu-frames", type=int, default=8192, help="oracle sample per point for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=1024, help="oracle sample per point per step (reference arm)")
@@ -661,6 +740,8 @@ def main(argv=None) -> int:
             bench_reference(args, rank, world)
         elif args.workload == "mixed":
             bench_mixed(args, rank, world, local_rank)
+        elif args.workload == "serve":
+            bench_serve(args, rank, world, local_rank)
         else:
             bench_ours(args, rank, world, local_rank)
     finally:
