@@ -649,7 +649,7 @@ def bench_serve(args, rank: int, world: int, local_rank: int) -> None:
 
     def summarize(out, arr, p):
         lat = out["latency"]
-        ok = lat >= 0
+        ok = np.isfinite(lat)
         t_end = out["report"]["seconds_to_last_completion"]
         R = arr.size
         bits = float(kmsg_pool[p[ok]].sum())
@@ -667,7 +667,7 @@ def bench_serve(args, rank: int, world: int, local_rank: int) -> None:
     for r_hz in (2e5, 5e5, 1e6, 1.5e6):
         req, arr, p = stream(r_hz, min(2.0, seconds), SERVE["seed"] + int(r_hz))
         out = ps.polar_serve(pset, req, arr, pool, pool_off, arena, wait_s=wait)
-        sweep.append(dict(offered_req_s=r_hz, **{k: v for k, v in summarize(out, arr, p).items() if k != "report"}))
+        sweep.append(dict(offered_req_s=r_hz, rc=out["rc"], **{k: v for k, v in summarize(out, arr, p).items() if k != "report"}))
     # the configured load served in full; both engines on the same prefix of it
     req, arr, p = stream(rate, seconds, SERVE["seed"])
     served = ps.polar_serve(pset, req, arr, pool, pool_off, arena, wait_s=wait)

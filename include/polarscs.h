@@ -251,7 +251,7 @@ int gsc_loss_grad_f64(const polar_plan *plan, const double *d_llr, const uint32_
  *  arrived requests are grouped by (plan, D, L) and each group is a separate
  *  scs_decode_batch launch.
  * Outputs per request: pm_out, status_out (as scs_decode_batch; 127 if never
- * decoded), latency_out (completion - arrival, seconds; -1 if not completed)
+ * decoded), latency_out (completion - arrival, seconds; NaN if not completed)
  * and, for polar_serve, the packed message words at info_off[r] of info_out
  * (both may be NULL).  report (6 doubles): seconds from start to the last
  * completion, arena-full stalls, error flag, most requests in flight (serve) or
