@@ -615,6 +615,100 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------ genie-aided SC (gradient)
+GSC = dict(N=1024, K=512, crc=0, frames=65536, ebn0=(2.0,), seed=4, design_snr_db=0.0, train_steps=200, lr=0.02,
+           fer_frames=1 << 18)
+
+
+def bench_gsc(args, rank: int, world: int, local_rank: int) -> None:
+    """Genie-aided SC with ten per-stage min-sum scales: forward + reverse
+    kernel throughput on 65,536 PC(1024,512) frames at 2.0 dB, a training run
+    of the scales with Adam, and the learned scales fed back into the
+    PC(1024,512) CRC-16 stack decoder (D = L = 32) against unit scales."""
+    import numpy as np
+    import torch
+
+    import paper_1809_03606_gb300 as ps
+
+    torch.cuda.set_device(local_rank)
+    ps.load(build_if_missing=True)
+    g = dict(GSC)
+    if args.frames:
+        g["frames"] = int(args.frames)
+    B, N, K = g["frames"], g["N"], g["K"]
+    n = N.bit_length() - 1
+    fr = ps.polar_construct(N, K, g["design_snr_db"])
+    plan = ps.Plan(N, K, fr, fast_nodes=False)
+    llrs, d_msg = make_gpu_inputs(ps, plan, B, rank, g)
+    x = llrs[0]
+    import workloads as W
+
+    msg = W.message_bits(rank_seed(rank, g), B, K)
+    u = torch.from_numpy(ps.u_from_messages(plan, msg)).cuda()
+    del msg
+    ones = torch.ones(n, dtype=torch.float32, device="cuda")
+
+    def step():
+        return ps.gsc_loss_grad(plan, x, u, ones)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.__enter__()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__(None, None, None)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = reduce_max(ms, world)
+
+    # training the scales (Adam), then the learned scales in the stack decoder
+    sc = torch.ones(n, dtype=torch.float32, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([sc], lr=g["lr"])
+    loss0 = None
+    for _ in range(g["train_steps"]):
+        opt.zero_grad()
+        loss = ps.genie_sc_loss(x, sc, u, plan)
+        loss.backward()
+        opt.step()
+        loss0 = loss.item() if loss0 is None else loss0
+    loss1 = ps.genie_sc_loss(x, sc.detach(), u, plan).item()
+    learned = sc.detach().cpu().numpy().astype(np.float32)
+
+    w = dict(WORKLOAD)
+    w["frames"] = g["fer_frames"]
+    w["ebn0"] = (2.0,)
+    dplan = ps.Plan(w["N"], w["K"], ps.polar_construct(w["N"], w["K"], w["design_snr_db"]), fast_nodes=True,
+                    crc=w["crc"])
+    dl, dmsg = make_gpu_inputs(ps, dplan, w["frames"], rank, w)
+    fer = {}
+    for name, scales in (("unit", None), ("learned", learned)):
+        dplan.set_scales(scales)
+        info, pm, st = ps.decode(dplan, dl[0], w["D"], w["L"])
+        torch.cuda.synchronize()
+        fer[name] = float((info != dmsg).any(dim=1).double().mean().item())
+    dplan.set_scales(None)
+    if rank == 0:
+        line = {"metric": "genie-aided SC forward+backward frames/s", "value": B * world / (ms / 1e3),
+                "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{B} frames of PC({N},{K}) at {g['ebn0'][0]} dB, genie-aided SC with {n} "
+                                       f"per-stage scales, loss and d loss/d scales per step",
+                           "loss_unit_scales": loss0, "loss_learned": loss1, "train_steps": g["train_steps"],
+                           "learned_scales": [round(float(v), 5) for v in learned],
+                           "scs_fer_check": {"workload": f"PC({w['N']},{w['K']}) CRC-{w['crc']} D={w['D']} "
+                                                         f"L={w['L']}, {w['frames']} frames at 2.0 dB",
+                                             "fer_unit_scales": fer["unit"], "fer_learned_scales": fer["learned"]}},
+                "clocks": sampler.summary() if sampler else None}
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ served workload
 SERVE = dict(rate=5e6, seconds=10.0, pool=1 << 18, seed=5, arena_bytes=2 << 30, interval_s=2e-3, compare_seconds=0.5)
 
@@ -710,9 +804,9 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "mixed", "serve"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "mixed", "serve", "gsc"], default="sweep",
                     help="sweep: the PC(1024,512) Eb/N0 sweep (default); mixed: the 2M-frame mixed batch; "
-                         "serve: Poisson-arrival serving")
+                         "serve: Poisson-arrival serving; gsc: genie-aided SC gradient and learned scales")
     ap.add_argument("--serve-rate", type=float, default=0.0, help="serve workload: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="serve workload: seconds of arrivals")
     ap.add_argument("--frames", type=int, default=0, help="frames per Eb/N0 point (default 1048576)")
@@ -742,6 +836,8 @@ def main(argv=None) -> int:
             bench_mixed(args, rank, world, local_rank)
         elif args.workload == "serve":
             bench_serve(args, rank, world, local_rank)
+        elif args.workload == "gsc":
+            bench_gsc(args, rank, world, local_rank)
         else:
             bench_ours(args, rank, world, local_rank)
     finally:

@@ -127,6 +127,65 @@ __device__ __forceinline__ float pen_transform(float x, int mode) {
     return (mode == 1) == neg ? fabsf(x) : 0.0f;
 }
 
+// Node reductions over more than 32 values (the few Rate-0, REP, Rate-1 and
+// SPC nodes above stage 5): out of line, so that the per-op code the warps
+// share stays small.
+
+// sum of the node's values (transformed by `mode`) in halving order; levels
+// wider than a warp are written into the free alpha stages below the node
+__device__ __noinline__ float node_sum_wide(float *alpha, const float *A, int len, int mode, int lane) {
+    int h = len >> 1;
+    float *dst = alpha + h;
+    for (int i = lane; i < h; i += 32) dst[i] = __fadd_rn(pen_transform(A[i], mode), pen_transform(A[i + h], mode));
+    __syncwarp();
+    const float *src = dst;
+    while (h > 32) {
+        h >>= 1;
+        float *d2 = alpha + h;
+        for (int i = lane; i < h; i += 32) d2[i] = __fadd_rn(src[i], src[i + h]);
+        __syncwarp();
+        src = d2;
+    }
+    float v = src[lane];
+    __syncwarp();
+    for (int k = 16; k >= 1; k >>= 1) {
+        const float o = __shfl_down_sync(FULL, v, k);
+        if (lane < k) v = __fadd_rn(v, o);
+    }
+    return __shfl_sync(FULL, v, 0);
+}
+
+struct Least {
+    int m[4];
+    float mag[4];
+};
+
+// the k least reliable of `len` > 32 values (|alpha|, ties to the lower index)
+__device__ __noinline__ Least node_least_wide(const float *A, int len, int k, int lane) {
+    Least r{{0, 0, 0, 0}, {0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (j >= k) break;
+        uint32_t bv = EMPTY, bi = EMPTY;
+        for (int i = lane; i < len; i += 32) {
+            bool used = false;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) used |= (q < j) && (r.m[q] == i);
+            if (used) continue;
+            const uint32_t v = __float_as_uint(fabsf(A[i]));
+            if (v < bv) {
+                bv = v;
+                bi = uint32_t(i);
+            }
+        }
+        const uint32_t gv = __reduce_min_sync(FULL, bv);
+        const uint32_t gi = __reduce_min_sync(FULL, bv == gv ? bi : EMPTY);
+        r.m[j] = int(gi);
+        r.mag[j] = __uint_as_float(gv);
+    }
+    return r;
+}
+
 struct Warp {
     const int lane;
     const int n;          // stage of the root
@@ -284,25 +343,7 @@ struct Warp {
             }
             return __shfl_sync(FULL, v, 0);
         }
-        int h = len >> 1;
-        float *dst = alpha + h;
-        for (int i = lane; i < h; i += 32) dst[i] = __fadd_rn(pen_transform(A[i], mode), pen_transform(A[i + h], mode));
-        __syncwarp();
-        const float *src = dst;
-        while (h > 32) {
-            h >>= 1;
-            float *d2 = alpha + h;
-            for (int i = lane; i < h; i += 32) d2[i] = __fadd_rn(src[i], src[i + h]);
-            __syncwarp();
-            src = d2;
-        }
-        float v = src[lane];
-        __syncwarp();
-        for (int k = 16; k >= 1; k >>= 1) {
-            const float o = __shfl_down_sync(FULL, v, k);
-            if (lane < k) v = __fadd_rn(v, o);
-        }
-        return __shfl_sync(FULL, v, 0);
+        return node_sum_wide(alpha, A, len, mode, lane);
     }
 
     // REP node of at most 32 values: S = sum alpha, and the penalties of the
@@ -331,7 +372,16 @@ struct Warp {
     __device__ void node_least(int lam, int k, int *m, float *mag) const {
         const int len = 1 << lam;
         const float *A = stage(lam);
-        if (len <= 32) {  // one value per lane: k rounds of warp minima
+        if (len > 32) {
+            const Least r = node_least_wide(A, len, k, lane);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                m[j] = r.m[j];
+                mag[j] = r.mag[j];
+            }
+            return;
+        }
+        {  // one value per lane: k rounds of warp minima
             uint32_t v = lane < len ? __float_as_uint(fabsf(A[lane])) : EMPTY;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -342,27 +392,6 @@ struct Warp {
                 mag[j] = __uint_as_float(gv);
                 if (uint32_t(lane) == gi) v = EMPTY;
             }
-            return;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j >= k) break;
-            uint32_t bv = EMPTY, bi = EMPTY;
-            for (int i = lane; i < len; i += 32) {
-                bool used = false;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) used |= (q < j) && (m[q] == i);
-                if (used) continue;
-                const uint32_t v = __float_as_uint(fabsf(A[i]));
-                if (v < bv) {
-                    bv = v;
-                    bi = uint32_t(i);
-                }
-            }
-            const uint32_t gv = __reduce_min_sync(FULL, bv);
-            const uint32_t gi = __reduce_min_sync(FULL, bv == gv ? bi : EMPTY);
-            m[j] = int(gi);
-            mag[j] = __uint_as_float(gv);
         }
     }
 
@@ -388,8 +417,11 @@ struct Warp {
     }
 };
 
+// The stack of one frame: entry j * 32 + lane lives in slot j of `lane`
+// (NS = 1 holds D <= 32 entries, NS = 2 up to 64).
+template <int NS>
 struct Stack {
-    uint32_t pm[2], meta[2], seq[2], aux[2];  // meta = len | sched << 16
+    uint32_t pm[NS], meta[NS], seq[NS], aux[NS];  // meta = len | sched << 16
 };
 
 __device__ __forceinline__ bool slot_exists(int j, int lane, int D) { return j * 32 + lane < D; }
@@ -469,57 +501,54 @@ __device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *
 // insert candidates 0..nc-1 in order (reading R11): free slots first, all at
 // once, then one by one, each replacing the worst entry (largest pm, ties:
 // oldest) only if its pm is strictly smaller
-__device__ __forceinline__ void insert_cands(Stack &st, int &count, const Cands &c, float pm, uint32_t meta,
+template <int NS>
+__device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Cands &c, float pm, uint32_t meta,
                                              uint32_t base, uint32_t slot, int D, int lane) {
     const int nfree = D - count;
     const int nb = c.nc < nfree ? c.nc : nfree;
     if (nb > 0) {
-        const bool f0 = st.pm[0] == EMPTY && slot_exists(0, lane, D);
-        const bool f1 = st.pm[1] == EMPTY && slot_exists(1, lane, D);
-        const uint32_t b0 = __ballot_sync(FULL, f0), b1 = __ballot_sync(FULL, f1);
         const uint32_t lt = (1u << lane) - 1u;
-        const int r0 = __popc(b0 & lt);
-        const int r1 = __popc(b0) + __popc(b1 & lt);
-        if (f0 && r0 < nb) {
-            st.pm[0] = __float_as_uint(__fadd_rn(pm, c.delta(r0)));
-            st.meta[0] = meta;
-            st.seq[0] = base + uint32_t(c.nc - 1 - r0);
-            st.aux[0] = slot | (c.mask(r0) << 8);
-        }
-        if (f1 && r1 < nb) {
-            st.pm[1] = __float_as_uint(__fadd_rn(pm, c.delta(r1)));
-            st.meta[1] = meta;
-            st.seq[1] = base + uint32_t(c.nc - 1 - r1);
-            st.aux[1] = slot | (c.mask(r1) << 8);
+        int before = 0;  // free slots in the rows above
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const bool f = st.pm[j] == EMPTY && slot_exists(j, lane, D);
+            const uint32_t bj = __ballot_sync(FULL, f);
+            const int r = before + __popc(bj & lt);
+            if (f && r < nb) {
+                st.pm[j] = __float_as_uint(__fadd_rn(pm, c.delta(r)));
+                st.meta[j] = meta;
+                st.seq[j] = base + uint32_t(c.nc - 1 - r);
+                st.aux[j] = slot | (c.mask(r) << 8);
+            }
+            before += __popc(bj);
         }
         count += nb;
     }
     for (int k = nb; k < c.nc; ++k) {
         const uint32_t pmb = __float_as_uint(__fadd_rn(pm, c.delta(k)));
-        const bool e0 = slot_exists(0, lane, D), e1 = slot_exists(1, lane, D);
+        const bool e0 = slot_exists(0, lane, D);
         uint32_t lw = e0 ? st.pm[0] : 0u, ls = e0 ? st.seq[0] : EMPTY;
         int lj = 0;
-        if (e1 && (st.pm[1] > lw || (st.pm[1] == lw && st.seq[1] < ls))) {
-            lw = st.pm[1];
-            ls = st.seq[1];
-            lj = 1;
-        }
+#pragma unroll
+        for (int j = 1; j < NS; ++j)
+            if (slot_exists(j, lane, D) && (st.pm[j] > lw || (st.pm[j] == lw && st.seq[j] < ls))) {
+                lw = st.pm[j];
+                ls = st.seq[j];
+                lj = j;
+            }
         const uint32_t gw = __reduce_max_sync(FULL, lw);
         const uint32_t gs = __reduce_min_sync(FULL, lw == gw ? ls : EMPTY);
         if (pmb < gw) {
             const uint32_t bal = __ballot_sync(FULL, lw == gw && ls == gs);
             if (lane == __ffs(bal) - 1) {
-                if (lj) {
-                    st.pm[1] = pmb;
-                    st.meta[1] = meta;
-                    st.seq[1] = base + uint32_t(c.nc - 1 - k);
-                    st.aux[1] = slot | (c.mask(k) << 8);
-                } else {
-                    st.pm[0] = pmb;
-                    st.meta[0] = meta;
-                    st.seq[0] = base + uint32_t(c.nc - 1 - k);
-                    st.aux[0] = slot | (c.mask(k) << 8);
-                }
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    if (lj == j) {
+                        st.pm[j] = pmb;
+                        st.meta[j] = meta;
+                        st.seq[j] = base + uint32_t(c.nc - 1 - k);
+                        st.aux[j] = slot | (c.mask(k) << 8);
+                    }
             }
         }
     }
@@ -527,10 +556,11 @@ __device__ __forceinline__ void insert_cands(Stack &st, int &count, const Cands 
 
 // a free snapshot slot among 0 .. D-1 (one always exists: the extended path
 // left the stack, so at most D - 1 snapshots are referenced)
-__device__ __forceinline__ int alloc_snapshot(const Stack &st, int D) {
+template <int NS>
+__device__ __forceinline__ int alloc_snapshot(const Stack<NS> &st, int D) {
     uint32_t lo = 0u, hi = 0u;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < NS; ++j) {
         if (st.pm[j] != EMPTY) {
             const uint32_t sn = st.aux[j] & 0xFFu;
             if (sn < 32u) lo |= 1u << sn;
@@ -559,6 +589,7 @@ __device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int
     __syncwarp();
 }
 
+template <int NS>
 __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Warp &w,
                                              unsigned b, uint32_t *orow) {
     const int lane = w.lane;
@@ -572,9 +603,9 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
     for (int i = lane; i < W; i += 32) w.beta[i] = 0u;
     __syncwarp();
 
-    Stack st;
+    Stack<NS> st;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < NS; ++j) {
         st.pm[j] = EMPTY;
         st.meta[j] = 0u;
         st.seq[j] = 0u;
@@ -620,11 +651,13 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         // ---- pop the best path: smallest pm, ties to the newest ----
         uint32_t lp = st.pm[0], ls = st.seq[0];
         int lj = 0;
-        if (D > 32 && (st.pm[1] < lp || (st.pm[1] == lp && st.pm[1] != EMPTY && st.seq[1] > ls))) {
-            lp = st.pm[1];
-            ls = st.seq[1];
-            lj = 1;
-        }
+#pragma unroll
+        for (int j = 1; j < NS; ++j)
+            if (st.pm[j] < lp || (st.pm[j] == lp && st.pm[j] != EMPTY && st.seq[j] > ls)) {
+                lp = st.pm[j];
+                ls = st.seq[j];
+                lj = j;
+            }
         const uint32_t gp = __reduce_min_sync(FULL, lp);
         if (gp == EMPTY) {  // count out of step with the slots: stop safely
             status = POLAR_TIMEOUT;
@@ -633,13 +666,20 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         const uint32_t gs = __reduce_max_sync(FULL, lp == gp ? ls : 0u);
         const uint32_t bal = __ballot_sync(FULL, lp == gp && ls == gs);
         const int wl = __ffs(bal) - 1;
-        const int wj = __shfl_sync(FULL, lj, wl);
         const uint32_t p_pmb = gp;
-        const uint32_t p_meta = __shfl_sync(FULL, wj ? st.meta[1] : st.meta[0], wl);
-        const uint32_t p_aux = __shfl_sync(FULL, wj ? st.aux[1] : st.aux[0], wl);
+        uint32_t my_meta = st.meta[0], my_aux = st.aux[0];  // this lane's best entry
+#pragma unroll
+        for (int j = 1; j < NS; ++j)
+            if (lj == j) {
+                my_meta = st.meta[j];
+                my_aux = st.aux[j];
+            }
+        const uint32_t p_meta = __shfl_sync(FULL, my_meta, wl);
+        const uint32_t p_aux = __shfl_sync(FULL, my_aux, wl);
         if (lane == wl) {
-            if (wj) st.pm[1] = EMPTY;
-            else st.pm[0] = EMPTY;
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                if (lj == j) st.pm[j] = EMPTY;
         }
         --count;
         ++n_iter;
@@ -727,21 +767,20 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
 
         // ---- alpha after a switch (Alg. calp): recompute the spine from the
         // channel, except the top stages the popped path shares with the
-        // spine held now (same node, identical beta before the node) ----
+        // spine held now (same node, identical beta before the node).  The
+        // recomputed stages rl .. lam_d run through the same op dispatch as
+        // the schedule walk below. ----
+        int rl = -1, lam_d = 0, s_d = 0;
         if (switched) {
             const uint32_t tgt = __ldg(&c.ops[p_sched].z);
             if (tgt != NO_TARGET) {
-                const int lam_d = int(tgt & 0xFFu);
-                const int s_d = int(tgt >> 8);
+                lam_d = int(tgt & 0xFFu);
+                s_d = int(tgt >> 8);
                 ops += 2u * uint32_t(N - (1 << lam_d));  // counted as the full recompute
                 int lam = n - 1;
                 while (lam >= lam_d && lam >= valid_lo && (s_d >> lam) == (cs >> lam) && div >= ((s_d >> lam) << lam))
                     --lam;
-                for (; lam >= lam_d; --lam) {
-                    const int sl = (s_d >> lam) << lam;
-                    if ((s_d >> lam) & 1) w.op_g(lam, sl);
-                    else w.op_f(lam);
-                }
+                rl = lam;
             }
         }
         PT(PH_ALPHA)
@@ -751,20 +790,33 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         int t = p_sched;
         const uint4 *opsv = reinterpret_cast<const uint4 *>(c.ops);
         uint4 nxt = __ldg(opsv + min(t, c.nops - 1));
-        for (; t < c.nops; ++t) {
-            const uint4 op = nxt;
-            if (t + 1 < c.nops) nxt = __ldg(opsv + t + 1);
-            const uint32_t code = op.x & 0xFFu;
-            const int lam = int((op.x >> 8) & 0xFFu);
-            const int s = int(op.y);
-            if (code >= OP_BRANCH) break;
+        uint4 op = nxt;
+        for (;;) {
+            uint32_t code;
+            int lam, s;
+            const bool sched = rl < lam_d;  // else: a recomputed spine stage
+            if (!sched) {
+                lam = rl;
+                s = (s_d >> lam) << lam;
+                code = ((s_d >> lam) & 1) ? OP_G : OP_F;
+                --rl;
+            } else {
+                if (t >= c.nops) break;
+                op = nxt;
+                if (t + 1 < c.nops) nxt = __ldg(opsv + t + 1);
+                code = op.x & 0xFFu;
+                lam = int((op.x >> 8) & 0xFFu);
+                s = int(op.y);
+                if (code >= OP_BRANCH) break;
+                ++t;
+            }
             if (code == OP_F) {
                 w.op_f(lam);
-                ops += 2u << lam;
+                if (sched) ops += 2u << lam;
                 PT(PH_FG)
             } else if (code == OP_G) {
                 w.op_g(lam, s);
-                ops += 2u << lam;
+                if (sched) ops += 2u << lam;
                 PT(PH_FG)
             } else if (code == OP_COMB) {
                 w.op_comb(lam, s);
@@ -779,94 +831,84 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             }
         }
         ++n_exp;
-        if (t == c.nops) {  // the path is complete: push it
-            const int slot = alloc_snapshot(st, D);
-            if (slot < 0) break;
-            write_snapshot(w, W, SW, slot, N, 0u, 0u, 0, 0);
-            cur_snap = uint32_t(slot);
-            applied = 0u;
-            beta_dirty = false;
-            cur_lo = valid_lo = n;
-            clam = n;
-            cs = 0;
-            ops += 1u + stack_cost;
-            Cands one{1, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
-            insert_cands(st, count, one, pm, uint32_t(N) | (uint32_t(c.nops) << 16), seq_next, uint32_t(slot), D, lane);
-            seq_next += 1u;
-            PT(PH_DONE)
-            continue;
-        }
 
-        // ---- branching node: visit counter and L-prune (Sec. 2.2.5) ----
-        const uint4 op = __ldg(opsv + t);
-        const uint32_t code = op.x & 0xFFu;
-        const int lam = int((op.x >> 8) & 0xFFu);
-        const int s = int(op.y);
-        const int len = 1 << lam;
-        uint32_t vc = 0;
-        if (lane == 0) vc = ++w.cnt[op.w];
-        vc = __shfl_sync(FULL, vc, 0);
-        __syncwarp();
-        if (int(vc) >= L) {
-            ops += stack_cost;
-            int removed = 0;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const bool kill = st.pm[j] != EMPTY && int(st.meta[j] & 0xFFFFu) <= s;
-                removed += __popc(__ballot_sync(FULL, kill));
-                if (kill) st.pm[j] = EMPTY;
-            }
-            count -= removed;
-        }
-        PT(PH_PRUNE)
-
-        // ---- node candidates (Sec. 2.2.4 and readings R7-R9) ----
+        // ---- the expansion's candidates: a complete path is pushed as it
+        // is; a branching node gets its visit counter, the L-prune
+        // (Sec. 2.2.5) and the node candidates (Sec. 2.2.4, readings R7-R9) ----
         Cands cd{0, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
         int m[4] = {0, 0, 0, 0};
-        if (code == OP_LEAF1) {
-            cd.mag[0] = fabsf(w.stage(0)[0]);
-            w.node_hd(0, s);
-            cd.nc = 2;
-            cd.masks = LEAF1_MASKS;
-            ops += 4u;
-        } else if (code == OP_REP) {
-            float S, p0;
-            uint32_t bbit;
-            if (len <= 32) {
-                float pz, po;
-                w.rep_sums(lam, S, pz, po);
-                bbit = S < 0.0f ? 1u : 0u;
-                p0 = bbit ? po : pz;
-            } else {
-                S = w.node_sum(lam, 0);
-                bbit = S < 0.0f ? 1u : 0u;
-                p0 = w.node_sum(lam, bbit ? 2 : 1);
+        int node_s = 0, node_lam = n, snap_lam = 0, nbits = N;
+        uint32_t meta = uint32_t(N) | (uint32_t(c.nops) << 16);
+        if (t >= c.nops) {
+            cd.nc = 1;
+            ops += 1u;
+        } else {
+            const uint32_t code = op.x & 0xFFu;
+            const int lam = int((op.x >> 8) & 0xFFu);
+            const int s = int(op.y);
+            const int len = 1 << lam;
+            node_s = s;
+            node_lam = snap_lam = lam;
+            nbits = s + len;
+            meta = uint32_t(s + len) | (uint32_t(t + 1) << 16);
+            uint32_t vc = 0;
+            if (lane == 0) vc = ++w.cnt[op.w];
+            vc = __shfl_sync(FULL, vc, 0);
+            __syncwarp();
+            if (int(vc) >= L) {
+                ops += stack_cost;
+                int removed = 0;
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    const bool kill = st.pm[j] != EMPTY && int(st.meta[j] & 0xFFFFu) <= s;
+                    removed += __popc(__ballot_sync(FULL, kill));
+                    if (kill) st.pm[j] = EMPTY;
+                }
+                count -= removed;
             }
-            w.set_range(lam, s, bbit);
-            cd.nc = 2;
-            cd.rep = true;
-            cd.rep0 = p0;
-            cd.rep1 = __fadd_rn(p0, fabsf(S));
-            ops += 4u * uint32_t(len) + 3u;
-        } else if (code == OP_R1) {
-            w.node_hd(lam, s);
-            w.node_least(lam, 2, m, cd.mag);
-            cd.nc = 4;
-            cd.masks = R1_MASKS;
-            ops += 6u * uint32_t(len) + 5u;
-        } else {  // OP_SPC
-            const uint32_t q = w.node_hd(lam, s);
-            w.node_least(lam, 4, m, cd.mag);
-            cd.nc = 8;
-            cd.masks = q ? SPC_MASKS_ODD : SPC_MASKS_EVEN;
-            ops += 10u * uint32_t(len) + (q ? 16u : 17u);
+            PT(PH_PRUNE)
+
+            if (code == OP_REP) {
+                float S, p0;
+                uint32_t bbit;
+                if (len <= 32) {
+                    float pz, po;
+                    w.rep_sums(lam, S, pz, po);
+                    bbit = S < 0.0f ? 1u : 0u;
+                    p0 = bbit ? po : pz;
+                } else {
+                    S = w.node_sum(lam, 0);
+                    bbit = S < 0.0f ? 1u : 0u;
+                    p0 = w.node_sum(lam, bbit ? 2 : 1);
+                }
+                w.set_range(lam, s, bbit);
+                cd.nc = 2;
+                cd.rep = true;
+                cd.rep0 = p0;
+                cd.rep1 = __fadd_rn(p0, fabsf(S));
+                ops += 4u * uint32_t(len) + 3u;
+            } else {  // information leaf, Rate-1 or SPC: hard decisions first
+                const uint32_t q = w.node_hd(lam, s);
+                if (code == OP_LEAF1) {
+                    cd.mag[0] = fabsf(w.stage(0)[0]);
+                    cd.nc = 2;
+                    cd.masks = LEAF1_MASKS;
+                    ops += 4u;
+                } else {
+                    const bool spc = code == OP_SPC;
+                    w.node_least(lam, spc ? 4 : 2, m, cd.mag);
+                    cd.nc = spc ? 8 : 4;
+                    cd.masks = spc ? (q ? SPC_MASKS_ODD : SPC_MASKS_EVEN) : R1_MASKS;
+                    ops += spc ? 10u * uint32_t(len) + (q ? 16u : 17u) : 6u * uint32_t(len) + 5u;
+                }
+            }
+            PT(PH_NODE)
         }
-        PT(PH_NODE)
 
         const int slot = alloc_snapshot(st, D);
         if (slot < 0) break;
-        write_snapshot(w, W, SW, slot, s + len, uint32_t(m[0]) | (uint32_t(m[1]) << 16),
-                       uint32_t(m[2]) | (uint32_t(m[3]) << 16), s, lam);
+        write_snapshot(w, W, SW, slot, nbits, uint32_t(m[0]) | (uint32_t(m[1]) << 16),
+                       uint32_t(m[2]) | (uint32_t(m[3]) << 16), node_s, snap_lam);
         cur_snap = uint32_t(slot);
         applied = 0u;
         beta_dirty = false;
@@ -874,12 +916,12 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         cm[1] = m[1];
         cm[2] = m[2];
         cm[3] = m[3];
-        cs = s;
-        clam = lam;
-        cur_lo = valid_lo = lam;
+        cs = node_s;
+        clam = node_lam;
+        cur_lo = valid_lo = node_lam;
         PT(PH_SNAP)
         ops += uint32_t(cd.nc) * stack_cost;
-        insert_cands(st, count, cd, pm, uint32_t(s + len) | (uint32_t(t + 1) << 16), seq_next, uint32_t(slot), D, lane);
+        insert_cands(st, count, cd, pm, meta, seq_next, uint32_t(slot), D, lane);
         seq_next += uint32_t(cd.nc);
         PT(PH_INSERT)
     }
@@ -915,7 +957,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
 // MIXED = false: every frame uses a.code, a.D, a.L and row b of the LLR and
 // message buffers.  MIXED = true: frame b has its own code, D and L
 // (a.frames[b]) and offsets into packed LLR and message buffers.
-template <bool MIXED>
+template <bool MIXED, int NS>
 __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Code codes_s[MIXED ? kMaxCodes : 1];
@@ -941,7 +983,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const Code &c = a.code;
                 Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                        my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
-                decode_frame(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
+                decode_frame<NS>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
             } else {
                 const int4 fd = a.frames[b];
                 if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
@@ -955,7 +997,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const long long lo = a.llr_off[b];
                 Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
                        reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales};
-                decode_frame(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
+                decode_frame<NS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
             }
         }
     }
@@ -977,6 +1019,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // of an earlier request there, a warp first copies its request's LLRs with
 // L2-only loads into its own staging area (its own stores keep its L1
 // coherent) and decodes from that copy.
+template <int NS>
 __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Code codes_s[kMaxCodes];
@@ -1024,7 +1067,7 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
             __syncwarp();
             Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                    my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
-            decode_frame(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
+            decode_frame<NS>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
         }
         if (lane == 0) {
             a.t_done[k] = global_ns();
@@ -1061,7 +1104,7 @@ Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, co
 int warp_smem_bytes(int N, int W, int nbranch) { return ((4 * N + 4 * W + nbranch) + 15) & ~15; }
 
 // block size and persistent grid for a kernel with `warp_smem` bytes per warp
-template <bool MIXED>
+template <bool MIXED, int NS>
 int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int *smem_out) {
     int dev = 0, sms = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1073,10 +1116,10 @@ int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int
     while (wpb > 1 && wpb * warp_smem + static_smem > max_smem) wpb >>= 1;
     if (wpb * warp_smem + static_smem > max_smem) return POLAR_ELIMIT;
     const int smem = wpb * warp_smem;
-    e = cudaFuncSetAttribute(scs_decode_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(scs_decode_kernel<MIXED, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel<MIXED>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel<MIXED, NS>, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return POLAR_ELIMIT;
     long long grid = (long long)sms * per_sm;
@@ -1107,7 +1150,8 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
 
     int grid = 0, wpb = 0, smem = 0;
-    int rc = launch_shape<false>(a.warp_smem, B, 4, &grid, &wpb, &smem);
+    int rc = D <= 32 ? launch_shape<false, 1>(a.warp_smem, B, 4, &grid, &wpb, &smem)
+                     : launch_shape<false, 2>(a.warp_smem, B, 4, &grid, &wpb, &smem);
     if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1121,7 +1165,8 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
     e = cudaMemsetAsync(ws, 0, 64, stream);
     if (e == cudaSuccess) {
-        scs_decode_kernel<false><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        if (D <= 32) scs_decode_kernel<false, 1><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        else scs_decode_kernel<false, 2><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(ws, stream);
@@ -1212,7 +1257,9 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     a.scratch_stride = (long long)(Dmax + 1) * (((set->Wmax + 4) + 7) & ~7);
 
     int grid = 0, wpb = 0, smem = 0;
-    int rc = launch_shape<true>(a.warp_smem, (B + chunk - 1) / chunk, wpb_pref, &grid, &wpb, &smem);
+    const int nb_units = (B + chunk - 1) / chunk;
+    int rc = Dmax <= 32 ? launch_shape<true, 1>(a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem)
+                        : launch_shape<true, 2>(a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem);
     if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1226,7 +1273,8 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
     e = cudaMemsetAsync(ws, 0, 64, stream);
     if (e == cudaSuccess) {
-        scs_decode_kernel<true><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        if (Dmax <= 32) scs_decode_kernel<true, 1><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        else scs_decode_kernel<true, 2><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(ws, stream);
@@ -1287,17 +1335,20 @@ int launch_scs_serve(const polar_plan_set *set, const void *codes_v, const int4 
     const int static_smem = int(sizeof(Code)) * kMaxCodes;
     while (wpb > 1 && wpb * a.warp_smem + static_smem > max_smem) wpb >>= 1;
     const int smem = wpb * a.warp_smem;
-    e = cudaFuncSetAttribute(scs_serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const void *kern = Dmax <= 32 ? reinterpret_cast<const void *>(scs_serve_kernel<1>)
+                                  : reinterpret_cast<const void *>(scs_serve_kernel<2>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_serve_kernel, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return POLAR_ELIMIT;
     long long grid = (long long)sms * per_sm;
     const size_t per_block = size_t(wpb) * size_t(a.scratch_stride) * 4;
     if (size_t(grid) * per_block > scratch_bytes) grid = (long long)(scratch_bytes / per_block);
     if (grid < 1) return POLAR_ENOMEM;
-    scs_serve_kernel<<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    if (Dmax <= 32) scs_serve_kernel<1><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    else scs_serve_kernel<2><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? 0 : cuda_status(e);
 }
@@ -1414,7 +1465,8 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     int wpb = 4;
     while (wpb > 1 && size_t(wpb) > warps_fit) wpb >>= 1;
     int grid = 0, smem = 0;
-    rc = launch_shape<false>(a.warp_smem, B, wpb, &grid, &wpb, &smem);
+    rc = D <= 32 ? launch_shape<false, 1>(a.warp_smem, B, wpb, &grid, &wpb, &smem)
+                 : launch_shape<false, 2>(a.warp_smem, B, wpb, &grid, &wpb, &smem);
     if (rc) return rc;
     const long long fit = (long long)(warps_fit / size_t(wpb));
     if (fit < grid) grid = int(fit);
@@ -1432,7 +1484,8 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
         e = cudaMemcpyAsync(tab + sc_off, p->scales.data(), sc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    scs_decode_kernel<false><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    if (D <= 32) scs_decode_kernel<false, 1><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    else scs_decode_kernel<false, 2><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? 0 : cuda_status(e);
 }
