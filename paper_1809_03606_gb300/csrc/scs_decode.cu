@@ -10,18 +10,25 @@
 //    memory scheme (stage lambda at float offset 2^lambda, the root stays in
 //    global memory and is read through L2), the in-place N-bit beta array
 //    (packed 32 bits per word) and the per-node visit counters.
-//  - The stack (D <= 64 entries) lives in registers, two entries per lane:
-//    path metric bits, length|schedule position, sequence number and a
-//    reference to a beta snapshot plus a flip mask.  Pop, worst-entry search
-//    and the L-prune are warp reductions (redux.sync).
+//  - The stack (D <= 64 entries) lives in registers, one entry per lane for
+//    D <= 32 and two for D <= 64: path metric bits, length|schedule
+//    position, sequence number and a reference to a beta snapshot plus a
+//    flip mask.  Pop, worst-entry search and the L-prune are warp reductions
+//    (redux.sync).
 //  - Each branching node writes ONE snapshot of the beta array (the hard
 //    decisions of the node in place) to scratch global memory; its 2-8
 //    candidates differ from it by flips of at most 4 positions (or all
 //    positions for REP), so a candidate costs registers only.  Snapshots are
 //    read back only on a path switch, after which the alpha spine is
 //    recomputed from the channel LLRs (Alg. calp).
+//  - The decode loop is kept small.  The warps of an SM sit in different
+//    parts of it and instruction fetch is their most frequent stall, so the
+//    lane-strided data loops are not unrolled and the rare paths (nodes wider
+//    than a warp, the restore after a path switch, CRC and output) are out of
+//    line.
 //  - All arithmetic on alpha and path metrics is float32 add/min/compare in
-//    the order of the reference definitions (no FMA: nothing here multiplies).
+//    the order of the reference definitions; the only products are the
+//    optional per-stage scales of f, rounded on their own (no FMA).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -136,12 +143,14 @@ __device__ __forceinline__ float pen_transform(float x, int mode) {
 __device__ __noinline__ float node_sum_wide(float *alpha, const float *A, int len, int mode, int lane) {
     int h = len >> 1;
     float *dst = alpha + h;
+    #pragma unroll 1
     for (int i = lane; i < h; i += 32) dst[i] = __fadd_rn(pen_transform(A[i], mode), pen_transform(A[i + h], mode));
     __syncwarp();
     const float *src = dst;
     while (h > 32) {
         h >>= 1;
         float *d2 = alpha + h;
+        #pragma unroll 1
         for (int i = lane; i < h; i += 32) d2[i] = __fadd_rn(src[i], src[i + h]);
         __syncwarp();
         src = d2;
@@ -153,6 +162,44 @@ __device__ __noinline__ float node_sum_wide(float *alpha, const float *A, int le
         if (lane < k) v = __fadd_rn(v, o);
     }
     return __shfl_sync(FULL, v, 0);
+}
+
+// path switch: the popped path's beta from its snapshot (the node's hard
+// decisions) with its flips applied; returns the first bit position where
+// it may differ from the beta it replaces (out of line)
+__device__ __noinline__ int restore_switch(const uint32_t *sp, uint32_t *beta, int W, uint32_t mask, int lane) {
+    const uint32_t m01 = sp[W], m23 = sp[W + 1];
+    const int ss = int(sp[W + 2]), slam = int(sp[W + 3]);
+    uint32_t dl = EMPTY;
+    #pragma unroll 1
+    for (int k = lane; k < W; k += 32) {
+        const uint32_t nv = sp[k];
+        const uint32_t x = nv ^ beta[k];
+        beta[k] = nv;
+        if (x && dl == EMPTY) dl = uint32_t(32 * k + __ffs(x) - 1);
+    }
+    dl = __reduce_min_sync(FULL, dl);
+    __syncwarp();
+    if (mask & FLIP_ALL) {
+        const int len = 1 << slam;
+        if (len >= 32) {
+            #pragma unroll 1
+            for (int k = lane; k < (len >> 5); k += 32) beta[(ss >> 5) + k] ^= FULL;
+        } else if (lane == 0) {
+            beta[ss >> 5] ^= ((1u << len) - 1u) << (ss & 31);
+        }
+    }
+    if (lane == 0) {
+        const int mm[4] = {int(m01 & 0xFFFFu), int(m01 >> 16), int(m23 & 0xFFFFu), int(m23 >> 16)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((mask >> j) & 1u) {
+                const int pos = ss + mm[j];
+                beta[pos >> 5] ^= 1u << (pos & 31);
+            }
+    }
+    __syncwarp();
+    return int(min(dl, uint32_t(ss)));  // the flips only touch [ss, ...)
 }
 
 struct Least {
@@ -167,6 +214,7 @@ __device__ __noinline__ Least node_least_wide(const float *A, int len, int k, in
     for (int j = 0; j < 4; ++j) {
         if (j >= k) break;
         uint32_t bv = EMPTY, bi = EMPTY;
+        #pragma unroll 1
         for (int i = lane; i < len; i += 32) {
             bool used = false;
 #pragma unroll
@@ -209,6 +257,7 @@ struct Warp {
         float *C = alpha + len;
         const float sv = scales ? __ldg(scales + lamc) : 1.0f;
         if (len >= 128 && vec_ok(lamc + 1)) {
+            #pragma unroll 1
             for (int i = 4 * lane; i < len; i += 128) {
                 const float4 x = *reinterpret_cast<const float4 *>(P + i);
                 const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
@@ -219,16 +268,8 @@ struct Warp {
                 r.w = __fmul_rn(sv, f_minsum(x.w, y.w));
                 *reinterpret_cast<float4 *>(C + i) = r;
             }
-        } else if (len >= 64 && vec_ok(lamc + 1)) {
-            for (int i = 2 * lane; i < len; i += 64) {
-                const float2 x = *reinterpret_cast<const float2 *>(P + i);
-                const float2 y = *reinterpret_cast<const float2 *>(P + i + len);
-                float2 r;
-                r.x = __fmul_rn(sv, f_minsum(x.x, y.x));
-                r.y = __fmul_rn(sv, f_minsum(x.y, y.y));
-                *reinterpret_cast<float2 *>(C + i) = r;
-            }
         } else {
+            #pragma unroll 1
             for (int i = lane; i < len; i += 32) C[i] = __fmul_rn(sv, f_minsum(P[i], P[i + len]));
         }
         __syncwarp();
@@ -242,6 +283,7 @@ struct Warp {
         const float *P = stage(lamc + 1);
         float *C = alpha + len;
         if (len >= 128 && vec_ok(lamc + 1)) {
+            #pragma unroll 1
             for (int i = 4 * lane; i < len; i += 128) {
                 const int pos = sl + i;  // a multiple of 4: the 4 bits share a word
                 const uint32_t bits = beta[pos >> 5] >> (pos & 31);
@@ -254,18 +296,8 @@ struct Warp {
                 r.w = g_op(x.w, y.w, (bits >> 3) & 1u);
                 *reinterpret_cast<float4 *>(C + i) = r;
             }
-        } else if (len >= 64 && vec_ok(lamc + 1)) {
-            for (int i = 2 * lane; i < len; i += 64) {
-                const int pos = sl + i;
-                const uint32_t bits = beta[pos >> 5] >> (pos & 31);
-                const float2 x = *reinterpret_cast<const float2 *>(P + i);
-                const float2 y = *reinterpret_cast<const float2 *>(P + i + len);
-                float2 r;
-                r.x = g_op(x.x, y.x, bits & 1u);
-                r.y = g_op(x.y, y.y, (bits >> 1) & 1u);
-                *reinterpret_cast<float2 *>(C + i) = r;
-            }
         } else {
+            #pragma unroll 1
             for (int i = lane; i < len; i += 32) {
                 const int pos = sl + i;
                 const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
@@ -281,6 +313,7 @@ struct Warp {
         const int sl = sr - len;
         if (len >= 32) {
             const int wl = sl >> 5, wr = sr >> 5, nw = len >> 5;
+            #pragma unroll 1
             for (int k = lane; k < nw; k += 32) beta[wl + k] ^= beta[wr + k];
         } else if (lane == 0) {
             const int w = sl >> 5, off = sl & 31;
@@ -296,6 +329,7 @@ struct Warp {
         const int len = 1 << lam;
         if (len >= 32) {
             const uint32_t v = bit ? FULL : 0u;
+            #pragma unroll 1
             for (int k = lane; k < (len >> 5); k += 32) beta[(s >> 5) + k] = v;
         } else if (lane == 0) {
             const uint32_t mask = ((1u << len) - 1u) << (s & 31);
@@ -400,6 +434,7 @@ struct Warp {
         if (mask & FLIP_ALL) {
             const int len = 1 << lam;
             if (len >= 32) {
+                #pragma unroll 1
                 for (int k = lane; k < (len >> 5); k += 32) beta[(s >> 5) + k] ^= FULL;
             } else if (lane == 0) {
                 beta[s >> 5] ^= ((1u << len) - 1u) << (s & 31);
@@ -456,6 +491,7 @@ __device__ __noinline__ bool crc_ok(const Code &c, const uint32_t *beta, int lan
     uint32_t syn = 0u;
     for (int r = 0; r < c.crc; ++r) {
         uint32_t par = 0u;
+        #pragma unroll 1
         for (int k = lane; k < c.W; k += 32) par ^= __popc(beta[k] & __ldg(c.crc_rows + size_t(r) * c.W + k));
         syn |= (par & 1u) << r;
     }
@@ -466,6 +502,7 @@ __device__ __noinline__ bool crc_ok(const Code &c, const uint32_t *beta, int lan
 // and read the message bits off the information set
 __device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *orow, int lane) {
     const int W = c.W, N = c.N;
+    #pragma unroll 1
     for (int k = lane; k < W; k += 32) {
         uint32_t x = u[k];
         if (N > 1) x ^= (x >> 1) & 0x55555555u;
@@ -477,10 +514,12 @@ __device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *
     }
     __syncwarp();
     for (int hw = 1; hw < W; hw <<= 1) {
+        #pragma unroll 1
         for (int k = lane; k < W; k += 32)
             if (!(k & hw)) u[k] ^= u[k + hw];
         __syncwarp();
     }
+    #pragma unroll 1
     for (int ow = lane; ow < c.info_words; ow += 32) {
         uint32_t word = 0u;
         for (int bb = 0; bb < 32; ++bb) {
@@ -579,6 +618,7 @@ __device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int
                                                uint32_t m23, int s, int lam) {
     uint32_t *sp = w.scr + size_t(slot) * SW;
     const int nw = min(W, (nbits + 31) >> 5);
+    #pragma unroll 1
     for (int k = w.lane; k < nw; k += 32) sp[k] = w.beta[k];
     if (w.lane == 0) {
         sp[W] = m01;
@@ -599,7 +639,9 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
     const uint32_t stack_cost = 2u * uint32_t(D > 2 ? 32 - __clz(D - 1) : 1);
 
     PT_INIT
+    #pragma unroll 1
     for (int i = lane; i < c.nbranch; i += 32) w.cnt[i] = 0;
+    #pragma unroll 1
     for (int i = lane; i < W; i += 32) w.beta[i] = 0u;
     __syncwarp();
 
@@ -703,6 +745,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         if (p_snap == cur_snap) {
             if (beta_dirty) {
                 const uint32_t *sp = w.scr + size_t(cur_snap) * SW;
+                #pragma unroll 1
                 for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
                 __syncwarp();
                 applied = 0u;
@@ -715,21 +758,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             switched = true;
             ++n_switch;
             ops += uint32_t(W);
-            const uint32_t *sp = w.scr + size_t(p_snap) * SW;
-            const uint32_t m01 = sp[W], m23 = sp[W + 1];
-            const int ss = int(sp[W + 2]), slam = int(sp[W + 3]);
-            uint32_t dl = EMPTY;
-            for (int k = lane; k < W; k += 32) {
-                const uint32_t nv = sp[k];
-                const uint32_t x = nv ^ w.beta[k];
-                w.beta[k] = nv;
-                if (x && dl == EMPTY) dl = uint32_t(32 * k + __ffs(x) - 1);
-            }
-            dl = __reduce_min_sync(FULL, dl);
-            div = int(min(dl, uint32_t(ss)));  // the flips below only touch [ss, ...)
-            const int mm[4] = {int(m01 & 0xFFFFu), int(m01 >> 16), int(m23 & 0xFFFFu), int(m23 >> 16)};
-            __syncwarp();
-            w.apply_flips(p_mask, mm, ss, slam);
+            div = restore_switch(w.scr + size_t(p_snap) * SW, w.beta, W, p_mask, lane);
             beta_dirty = true;
         }
         PT(PH_BETA)
@@ -752,6 +781,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
                 have_first = true;
                 first_pm = __uint_as_float(p_pmb);
                 uint32_t *sp = w.scr + size_t(D) * SW;
+                #pragma unroll 1
                 for (int k = lane; k < W; k += 32) sp[k] = w.beta[k];
                 __syncwarp();
             }
@@ -929,8 +959,10 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
     // ---- output ----
     if (out_src == 2) {
         const uint32_t *sp = w.scr + size_t(D) * SW;
+        #pragma unroll 1
         for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
     } else if (out_src == 0) {
+        #pragma unroll 1
         for (int k = lane; k < W; k += 32) w.beta[k] = 0u;
     }
     __syncwarp();
@@ -1063,6 +1095,7 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
             const Code &c = codes_s[fd.x];
             const float *src = a.llr + a.llr_off[k];
             float *stage = reinterpret_cast<float *>(scr + a.serve_stage_off);
+            #pragma unroll 1
             for (int i = lane; i < c.N; i += 32) stage[i] = __ldcg(src + i);
             __syncwarp();
             Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
