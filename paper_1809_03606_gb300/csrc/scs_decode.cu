@@ -202,6 +202,53 @@ __device__ __noinline__ int restore_switch(const uint32_t *sp, uint32_t *beta, i
     return int(min(dl, uint32_t(ss)));  // the flips only touch [ss, ...)
 }
 
+// f and g from the channel LLRs (the root stage, in global memory), out of
+// line: vector loads when the rows are 16-byte aligned
+__device__ __noinline__ void f_root(const float *P, float *C, int len, float sv, int vec, int lane) {
+    if (vec && len >= 128) {
+        #pragma unroll 1
+        for (int i = 4 * lane; i < len; i += 128) {
+            const float4 x = *reinterpret_cast<const float4 *>(P + i);
+            const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
+            float4 r;
+            r.x = __fmul_rn(sv, f_minsum(x.x, y.x));
+            r.y = __fmul_rn(sv, f_minsum(x.y, y.y));
+            r.z = __fmul_rn(sv, f_minsum(x.z, y.z));
+            r.w = __fmul_rn(sv, f_minsum(x.w, y.w));
+            *reinterpret_cast<float4 *>(C + i) = r;
+        }
+    } else {
+        #pragma unroll 1
+        for (int i = lane; i < len; i += 32) C[i] = __fmul_rn(sv, f_minsum(P[i], P[i + len]));
+    }
+}
+
+__device__ __noinline__ void g_root(const float *P, float *C, const uint32_t *beta, int len, int sl, int vec,
+                                    int lane) {
+    if (vec && len >= 128) {
+        #pragma unroll 1
+        for (int i = 4 * lane; i < len; i += 128) {
+            const int pos = sl + i;
+            const uint32_t bits = beta[pos >> 5] >> (pos & 31);
+            const float4 x = *reinterpret_cast<const float4 *>(P + i);
+            const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
+            float4 r;
+            r.x = g_op(x.x, y.x, bits & 1u);
+            r.y = g_op(x.y, y.y, (bits >> 1) & 1u);
+            r.z = g_op(x.z, y.z, (bits >> 2) & 1u);
+            r.w = g_op(x.w, y.w, (bits >> 3) & 1u);
+            *reinterpret_cast<float4 *>(C + i) = r;
+        }
+    } else {
+        #pragma unroll 1
+        for (int i = lane; i < len; i += 32) {
+            const int pos = sl + i;
+            const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
+            C[i] = g_op(P[i], P[i + len], bit);
+        }
+    }
+}
+
 struct Least {
     int m[4];
     float mag[4];
@@ -246,17 +293,21 @@ struct Warp {
     const float *scales;  // f output scale per stage, or null (plain min-sum)
 
     __device__ const float *stage(int lam) const { return lam == n ? root : alpha + (1 << lam); }
-    __device__ bool vec_ok(int plam) const { return plam < n || llr_vec; }
 
     // alpha of the even child (lamc) from its parent (Eq. llrcalc, f); every
     // f output is multiplied by the stage scale (1.0, an exact identity, for
     // plain min-sum)
     __device__ void op_f(int lamc) const {
         const int len = 1 << lamc;
-        const float *P = stage(lamc + 1);
         float *C = alpha + len;
         const float sv = scales ? __ldg(scales + lamc) : 1.0f;
-        if (len >= 128 && vec_ok(lamc + 1)) {
+        if (lamc + 1 == n) {
+            f_root(root, C, len, sv, llr_vec, lane);
+            __syncwarp();
+            return;
+        }
+        const float *P = alpha + 2 * len;
+        if (len >= 128) {
             #pragma unroll 1
             for (int i = 4 * lane; i < len; i += 128) {
                 const float4 x = *reinterpret_cast<const float4 *>(P + i);
@@ -280,9 +331,14 @@ struct Warp {
     __device__ void op_g(int lamc, int sc) const {
         const int len = 1 << lamc;
         const int sl = sc - len;
-        const float *P = stage(lamc + 1);
         float *C = alpha + len;
-        if (len >= 128 && vec_ok(lamc + 1)) {
+        if (lamc + 1 == n) {
+            g_root(root, C, beta, len, sl, llr_vec, lane);
+            __syncwarp();
+            return;
+        }
+        const float *P = alpha + 2 * len;
+        if (len >= 128) {
             #pragma unroll 1
             for (int i = 4 * lane; i < len; i += 128) {
                 const int pos = sl + i;  // a multiple of 4: the 4 bits share a word
