@@ -353,7 +353,8 @@ def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
     else:
         roof = {"bound": "hbm", "achieved": bytes_step / kernel_s / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None if traffic_pf is None else float(sum(traffic_pf)) * B  # bytes per step (all launches)
+    # DRAM bytes per launch (ncu), averaged over the step's launches like `achieved`
+    roof["traffic"] = None if traffic_pf is None else float(sum(traffic_pf)) * B / npts
     roof["peak_source"] = (f"{peaks['source']}: {sms} SMs x {ALU_LANES_PER_SM} lanes x {peaks['sm_max_mhz']:.0f} MHz"
                            if roof["bound"] == "alu" else f"{peaks['source']} HBM copy bandwidth")
     per_point = []

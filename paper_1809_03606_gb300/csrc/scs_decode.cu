@@ -619,21 +619,31 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
         }
         count += nb;
     }
+    // the worst entry's metric is found again only after a replacement (a
+    // rejected candidate leaves the stack as it was)
+    uint32_t lw = 0u, ls = EMPTY, gw = 0u;
+    int lj = 0;
+    bool stale = true;
     for (int k = nb; k < c.nc; ++k) {
         const uint32_t pmb = __float_as_uint(__fadd_rn(pm, c.delta(k)));
-        const bool e0 = slot_exists(0, lane, D);
-        uint32_t lw = e0 ? st.pm[0] : 0u, ls = e0 ? st.seq[0] : EMPTY;
-        int lj = 0;
+        if (stale) {
+            const bool e0 = slot_exists(0, lane, D);
+            lw = e0 ? st.pm[0] : 0u;
+            ls = e0 ? st.seq[0] : EMPTY;
+            lj = 0;
 #pragma unroll
-        for (int j = 1; j < NS; ++j)
-            if (slot_exists(j, lane, D) && (st.pm[j] > lw || (st.pm[j] == lw && st.seq[j] < ls))) {
-                lw = st.pm[j];
-                ls = st.seq[j];
-                lj = j;
-            }
-        const uint32_t gw = __reduce_max_sync(FULL, lw);
-        const uint32_t gs = __reduce_min_sync(FULL, lw == gw ? ls : EMPTY);
+            for (int j = 1; j < NS; ++j)
+                if (slot_exists(j, lane, D) && (st.pm[j] > lw || (st.pm[j] == lw && st.seq[j] < ls))) {
+                    lw = st.pm[j];
+                    ls = st.seq[j];
+                    lj = j;
+                }
+            gw = __reduce_max_sync(FULL, lw);
+            stale = false;
+        }
         if (pmb < gw) {
+            stale = true;
+            const uint32_t gs = __reduce_min_sync(FULL, lw == gw ? ls : EMPTY);
             const uint32_t bal = __ballot_sync(FULL, lw == gw && ls == gs);
             if (lane == __ffs(bal) - 1) {
 #pragma unroll
