@@ -55,11 +55,15 @@ def _load():
             lib.or_crc.argtypes = [u8p, C.c_int, C.c_int]
             lib.or_crc.restype = C.c_uint32
             lib.or_encode_msg.argtypes = [u8p, C.c_int, C.c_int, u8p, C.c_int, u8p]
+            lib.or_encode_sys.argtypes = [u8p, C.c_int, u8p, u8p]
+            lib.or_encode_msg_sys.argtypes = [u8p, C.c_int, C.c_int, u8p, C.c_int, u8p]
             lib.or_schedule.argtypes = [C.c_int, u8p, C.c_int, i32p, C.c_int]
             lib.or_scs_decode.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, u8p, f32p, u8p, u64p]
             lib.or_scs_decode_batch.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, u8p, f32p, i8p, u64p]
             lib.or_scs_decode_s.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, u8p, f32p, u8p, u64p]
             lib.or_scs_decode_batch_s.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, u8p, f32p, i8p, u64p]
+            lib.or_scs_decode_sx.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, C.c_int, u8p, f32p, u8p, u64p]
+            lib.or_scs_decode_batch_sx.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, C.c_int, u8p, f32p, i8p, u64p]
             lib.or_scs_decode_exact.argtypes = [f64p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, u8p, f64p]
             lib.or_gsc_forward.argtypes = [f64p, u8p, C.c_int, f64p, f64p]
             lib.or_gsc_loss_grad.argtypes = [f64p, u8p, C.c_int, C.c_int, u8p, f64p, f64p, f64p]
@@ -97,21 +101,35 @@ def crc(bits: np.ndarray, crc_len: int) -> int:
     return int(_load().or_crc(_p(bits, C.c_uint8), bits.size, crc_len))
 
 
-def encode_msg(msg: np.ndarray, N: int, K: int, frozen: np.ndarray, crc_len: int = 0) -> np.ndarray:
+def encode_sys(info: np.ndarray, N: int, frozen: np.ndarray) -> np.ndarray:
+    """Systematic codeword: x = u F^{(x)n}, u frozen = 0, x on the information
+    set = the K bits of ``info`` in increasing index order."""
+    info, fr = _u8(info), _u8(frozen)
+    x = np.zeros(N, np.uint8)
+    rc = _load().or_encode_sys(_p(info, C.c_uint8), N, _p(fr, C.c_uint8), _p(x, C.c_uint8))
+    if rc:
+        raise ValueError(f"or_encode_sys -> {rc}")
+    return x
+
+
+def encode_msg(msg: np.ndarray, N: int, K: int, frozen: np.ndarray, crc_len: int = 0,
+               systematic: bool = False) -> np.ndarray:
     """Codeword for one message of K - crc bits (CRC appended MSB first)."""
     msg, fr = _u8(msg), _u8(frozen)
     cw = np.zeros(N, np.uint8)
-    rc = _load().or_encode_msg(_p(msg, C.c_uint8), N, K, _p(fr, C.c_uint8), crc_len, _p(cw, C.c_uint8))
+    fn = _load().or_encode_msg_sys if systematic else _load().or_encode_msg
+    rc = fn(_p(msg, C.c_uint8), N, K, _p(fr, C.c_uint8), crc_len, _p(cw, C.c_uint8))
     if rc:
         raise ValueError(f"or_encode_msg -> {rc}")
     return cw
 
 
-def encode_batch(msgs: np.ndarray, N: int, K: int, frozen: np.ndarray, crc_len: int = 0) -> np.ndarray:
+def encode_batch(msgs: np.ndarray, N: int, K: int, frozen: np.ndarray, crc_len: int = 0,
+                 systematic: bool = False) -> np.ndarray:
     msgs = _u8(msgs)
     out = np.zeros((msgs.shape[0], N), np.uint8)
     for b in range(msgs.shape[0]):
-        out[b] = encode_msg(msgs[b], N, K, frozen, crc_len)
+        out[b] = encode_msg(msgs[b], N, K, frozen, crc_len, systematic)
     return out
 
 
@@ -134,9 +152,10 @@ def _scales_arg(scales):
 
 
 def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: bool, D: int, L: int, crc_len: int = 0,
-               scales=None):
+               scales=None, systematic: bool = False):
     """One frame.  Returns (status, msg bits [K-crc], pm, codeword [N], stats dict).
-    ``scales`` (n floats) multiplies every f output written at stage lambda."""
+    ``scales`` (n floats) multiplies every f output written at stage lambda;
+    ``systematic`` reads the message off the codeword estimate."""
     llr = np.ascontiguousarray(llr, dtype=np.float32)
     fr = _u8(frozen)
     msg = np.zeros(K - crc_len, np.uint8)
@@ -144,8 +163,9 @@ def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: boo
     pm = C.c_float(0.0)
     st = np.zeros(5, np.uint64)
     sc, scp = _scales_arg(scales)
-    rc = _load().or_scs_decode_s(_p(llr, C.c_float), N, K, _p(fr, C.c_uint8), int(bool(fast)), D, L, crc_len, scp,
-                                 _p(msg, C.c_uint8), C.byref(pm), _p(cw, C.c_uint8), _p(st, C.c_uint64))
+    rc = _load().or_scs_decode_sx(_p(llr, C.c_float), N, K, _p(fr, C.c_uint8), int(bool(fast)), D, L, crc_len, scp,
+                                  int(bool(systematic)), _p(msg, C.c_uint8), C.byref(pm), _p(cw, C.c_uint8),
+                                  _p(st, C.c_uint64))
     if rc < 0:
         raise ValueError(f"or_scs_decode -> {rc}")
     stats = dict(iterations=int(st[0]), switches=int(st[1]), ops=int(st[2]), expansions=int(st[3]), max_visits=int(st[4]))
@@ -153,7 +173,7 @@ def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: boo
 
 
 def scs_decode_batch(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: bool, D: int, L: int,
-                     crc_len: int = 0, threads: int = 1, scales=None):
+                     crc_len: int = 0, threads: int = 1, scales=None, systematic: bool = False):
     """B frames (rows of llr).  Returns (msg [B,K-crc] u8, pm [B] f32, status [B] i8, stats [B,4] u64).
 
     ``threads`` > 1 splits the frames into contiguous chunks decoded by host
@@ -172,9 +192,10 @@ def scs_decode_batch(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fas
     def run(lo, hi):
         if hi <= lo:
             return 0
-        return lib.or_scs_decode_batch_s(_p(llr[lo:hi], C.c_float), hi - lo, N, K, _p(fr, C.c_uint8), int(bool(fast)),
-                                         D, L, crc_len, scp, _p(msg[lo:hi], C.c_uint8), _p(pm[lo:hi], C.c_float),
-                                         _p(status[lo:hi], C.c_int8), _p(stats[lo:hi], C.c_uint64))
+        return lib.or_scs_decode_batch_sx(_p(llr[lo:hi], C.c_float), hi - lo, N, K, _p(fr, C.c_uint8),
+                                          int(bool(fast)), D, L, crc_len, scp, int(bool(systematic)),
+                                          _p(msg[lo:hi], C.c_uint8), _p(pm[lo:hi], C.c_float),
+                                          _p(status[lo:hi], C.c_int8), _p(stats[lo:hi], C.c_uint64))
 
     threads = max(1, min(int(threads), B))
     if threads == 1:

@@ -49,6 +49,10 @@
  *   R14 CRC: init 0, no reflection, no final xor, MSB first over the message
  *       bits in increasing info-index order; the CRC occupies the last crc
  *       info positions.
+ * Systematic encoding (Sec. 2.2.2, Sec. 4): the codeword itself carries the
+ * K information bits on the information set A, x_A = info, with u frozen = 0
+ * and x = u F^{(x)n}; the decoder then reads the message straight from the
+ * final beta array instead of re-encoding it.
  * Optional scaled min-sum (not in the paper; the learnable form of the
  * genie-aided gradient below): every f output written at stage lambda is
  * multiplied by scales[lambda] in float32.
@@ -204,6 +208,56 @@ int or_encode_msg(const uint8_t *msg, int N, int K, const uint8_t *frozen, int c
     return OR_OK;
 }
 
+/* Systematic encoding by its definition: find u with u_i = 0 off A and   */
+/* (u F^{(x)n})_j = info_j on A.  F^{(x)n} has a 1 at (i, j) iff the bits  */
+/* of j are a subset of those of i, so x_j = XOR of u_i over i containing  */
+/* j: a unit triangular system, solved from the largest index of A down.  */
+int or_encode_sys(const uint8_t *info, int N, const uint8_t *frozen, uint8_t *x) {
+    if (!is_pow2(N)) return OR_EINVAL;
+    uint8_t *u = (uint8_t *)calloc(N, 1);
+    int *pos = (int *)malloc(sizeof(int) * N);
+    if (!u || !pos) {
+        free(u);
+        free(pos);
+        return OR_ENOMEM;
+    }
+    int K = 0;
+    for (int i = 0; i < N; i++)
+        if (!frozen[i]) pos[K++] = i;
+    for (int k = K - 1; k >= 0; k--) {
+        int j = pos[k];
+        uint8_t acc = info[k] & 1;
+        for (int t = k + 1; t < K; t++) {
+            int i = pos[t];
+            if ((i & j) == j) acc ^= u[i];
+        }
+        u[j] = acc;
+    }
+    or_encode(u, N, x);
+    free(u);
+    free(pos);
+    return OR_OK;
+}
+
+/* message + CRC (as in or_encode_msg) placed systematically */
+int or_encode_msg_sys(const uint8_t *msg, int N, int K, const uint8_t *frozen, int crc, uint8_t *codeword) {
+    if (!is_pow2(N) || K < 1 || K > N || crc < 0 || crc >= K || (crc && !crc_poly(crc))) return OR_EINVAL;
+    int nf = 0;
+    for (int i = 0; i < N; i++) nf += frozen[i] ? 1 : 0;
+    if (nf != N - K) return OR_EINVAL;
+    int Kmsg = K - crc;
+    uint8_t *info = (uint8_t *)malloc(K);
+    if (!info) return OR_ENOMEM;
+    for (int j = 0; j < Kmsg; j++) info[j] = msg[j] & 1;
+    if (crc) {
+        uint32_t reg = or_crc(msg, Kmsg, crc);
+        for (int j = 0; j < crc; j++) info[Kmsg + j] = (reg >> (crc - 1 - j)) & 1u;
+    }
+    int rc = or_encode_sys(info, N, frozen, codeword);
+    free(info);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Schedule (Sec. 3.1, Fig. fsscsch): built once per code by walking the    */
 /* tree; a node is either decoded by its node operation or split into       */
@@ -307,6 +361,7 @@ typedef struct {
     uint8_t *xhat, *uhat, *first_bits;
     uint64_t st_iter, st_switch, st_ops, st_exp, st_maxcnt;
     int stack_cost;
+    int systematic; /* message read from the codeword estimate (no re-encode) */
 } or_dec;
 
 static void dec_free(or_dec *d) {
@@ -458,12 +513,17 @@ static void stack_prune(or_dec *d, int omega) {
 }
 
 /* message bits of a codeword estimate: re-encode (F is an involution, Sec. */
-/* 2.2.2) and read the information set in increasing index order           */
+/* 2.2.2) and read the information set in increasing index order; with    */
+/* systematic encoding they are the codeword bits on the information set  */
 static void extract_info(or_dec *d, const uint8_t *xhat, uint8_t *info /* K */) {
-    or_encode(xhat, d->N, d->uhat);
+    const uint8_t *src = xhat;
+    if (!d->systematic) {
+        or_encode(xhat, d->N, d->uhat);
+        src = d->uhat;
+    }
     int k = 0;
     for (int i = 0; i < d->N; i++)
-        if (!d->frozen[i]) info[k++] = d->uhat[i];
+        if (!d->frozen[i]) info[k++] = src[i];
 }
 
 static int crc_passes(or_dec *d, const uint8_t *xhat) {
@@ -591,7 +651,7 @@ static void write_output(or_dec *d, const uint8_t *xhat, uint8_t *msg_out, uint8
     extract_info(d, xhat, info);
     if (msg_out) memcpy(msg_out, info, (size_t)d->Kmsg);
     if (cw_out) memcpy(cw_out, xhat, (size_t)d->N);
-    d->st_ops += (uint64_t)d->n * (uint64_t)words32(d->N);
+    if (!d->systematic) d->st_ops += (uint64_t)d->n * (uint64_t)words32(d->N);
 }
 
 /* FSSCS-RM search (Sec. 2.2.5, Sec. 3.3, Sec. 4) for one frame. */
@@ -702,12 +762,14 @@ static int scs_run(or_dec *d, const float *llr, uint8_t *msg_out, float *pm_out,
 
 /* stats (optional, 5 entries): pops, path switches, counted ops, expansions,
  * largest number of paths that branched at one node */
-int or_scs_decode_s(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
-                    const float *scales, uint8_t *msg_out, float *pm_out, uint8_t *cw_out, uint64_t *stats) {
+int or_scs_decode_sx(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
+                     const float *scales, int systematic, uint8_t *msg_out, float *pm_out, uint8_t *cw_out,
+                     uint64_t *stats) {
     or_dec d;
     int rc = dec_init(&d, N, K, frozen, fast, D, L, crc);
     if (rc) return rc;
     d.scales = scales;
+    d.systematic = systematic ? 1 : 0;
     float pm = 0.0f;
     rc = scs_run(&d, llr, msg_out, &pm, cw_out);
     if (pm_out) *pm_out = pm;
@@ -722,6 +784,11 @@ int or_scs_decode_s(const float *llr, int N, int K, const uint8_t *frozen, int f
     return rc;
 }
 
+int or_scs_decode_s(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
+                    const float *scales, uint8_t *msg_out, float *pm_out, uint8_t *cw_out, uint64_t *stats) {
+    return or_scs_decode_sx(llr, N, K, frozen, fast, D, L, crc, scales, 0, msg_out, pm_out, cw_out, stats);
+}
+
 int or_scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
                   uint8_t *msg_out, float *pm_out, uint8_t *cw_out, uint64_t *stats) {
     return or_scs_decode_s(llr, N, K, frozen, fast, D, L, crc, NULL, msg_out, pm_out, cw_out, stats);
@@ -729,13 +796,14 @@ int or_scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int fas
 
 /* B frames, row-major llr[B][N]; msg_out[B][K-crc]; stats_out[B][4] optional
  * (iterations, switches, counted ops, expansions) */
-int or_scs_decode_batch_s(const float *llr, int B, int N, int K, const uint8_t *frozen, int fast, int D, int L,
-                          int crc, const float *scales, uint8_t *msg_out, float *pm_out, int8_t *status_out,
-                          uint64_t *stats_out) {
+int or_scs_decode_batch_sx(const float *llr, int B, int N, int K, const uint8_t *frozen, int fast, int D, int L,
+                           int crc, const float *scales, int systematic, uint8_t *msg_out, float *pm_out,
+                           int8_t *status_out, uint64_t *stats_out) {
     or_dec d;
     int rc = dec_init(&d, N, K, frozen, fast, D, L, crc);
     if (rc) return rc;
     d.scales = scales;
+    d.systematic = systematic ? 1 : 0;
     for (int b = 0; b < B; b++) {
         float pm = 0.0f;
         int st = scs_run(&d, llr + (size_t)b * N, msg_out ? msg_out + (size_t)b * (K - crc) : NULL, &pm, NULL);
@@ -750,6 +818,13 @@ int or_scs_decode_batch_s(const float *llr, int B, int N, int K, const uint8_t *
     }
     dec_free(&d);
     return OR_OK;
+}
+
+int or_scs_decode_batch_s(const float *llr, int B, int N, int K, const uint8_t *frozen, int fast, int D, int L,
+                          int crc, const float *scales, uint8_t *msg_out, float *pm_out, int8_t *status_out,
+                          uint64_t *stats_out) {
+    return or_scs_decode_batch_sx(llr, B, N, K, frozen, fast, D, L, crc, scales, 0, msg_out, pm_out, status_out,
+                                  stats_out);
 }
 
 int or_scs_decode_batch(const float *llr, int B, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
