@@ -36,12 +36,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(N=1024, K=512, crc=16, D=32, L=32, fast=True, frames=1 << 20, ebn0=(1.5, 2.0, 2.5, 3.0), seed=2,
-                design_snr_db=0.0)
+                design_snr_db=0.0, systematic=False)
 ALU_LANES_PER_SM = 128  # FP32/INT32 lanes per SM (4 partitions x 32)
 
 
 def workload_name(w=WORKLOAD) -> str:
-    return (f"PC({w['N']},{w['K']}) CRC-{w['crc']} FSSCS-RM D={w['D']} L={w['L']} fast nodes, "
+    sysd = "systematic " if w.get("systematic") else ""
+    return (f"{sysd}PC({w['N']},{w['K']}) CRC-{w['crc']} FSSCS-RM D={w['D']} L={w['L']} fast nodes, "
             f"{w['frames']} frames x Eb/N0 {'/'.join(str(e) for e in w['ebn0'])} dB")
 
 
@@ -215,7 +216,7 @@ def oracle_sample_inputs(frames: int, rank: int, w=WORKLOAD):
     fr = oracle.construct(w["N"], w["K"], w["design_snr_db"])
     kmsg = w["K"] - w["crc"]
     msg = W.message_bits(seed, frames, kmsg)
-    cw = oracle.encode_batch(msg, w["N"], w["K"], fr, w["crc"])
+    cw = oracle.encode_batch(msg, w["N"], w["K"], fr, w["crc"], systematic=bool(w.get("systematic")))
     z = W.awgn_noise(seed, frames, w["N"])
     llrs = [W.bpsk_awgn_llr(cw, z, W.sigma_from_ebn0(e, w["K"] / w["N"])) for e in w["ebn0"]]
     return fr, msg, llrs
@@ -226,7 +227,7 @@ def run_oracle(fr, llrs, threads: int, w=WORKLOAD):
 
     t0 = time.perf_counter()
     outs = [oracle.scs_decode_batch(l, w["N"], w["K"], fr, fast=w["fast"], D=w["D"], L=w["L"], crc_len=w["crc"],
-                                    threads=threads) for l in llrs]
+                                    threads=threads, systematic=bool(w.get("systematic"))) for l in llrs]
     return time.perf_counter() - t0, outs
 
 
@@ -240,12 +241,13 @@ def bench_reference(args, rank: int, world: int) -> None:
 
     sample = args.ref_frames
     threads = os.cpu_count() or 1
-    fr, msg, llrs = oracle_sample_inputs(sample, 0)
+    w = dict(WORKLOAD, systematic=bool(args.systematic))
+    fr, msg, llrs = oracle_sample_inputs(sample, 0, w)
     for _ in range(args.warmup):
-        run_oracle(fr, llrs, threads)
+        run_oracle(fr, llrs, threads, w)
     times = []
     for _ in range(args.steps):
-        dt, outs = run_oracle(fr, llrs, threads)
+        dt, outs = run_oracle(fr, llrs, threads, w)
         times.append(dt)
     kmsg = WORKLOAD["K"] - WORKLOAD["crc"]
     total = sum(times)
@@ -256,7 +258,7 @@ def bench_reference(args, rank: int, world: int) -> None:
     line = {"impl": "reference", "metric": "decoded info Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(), "sample": desc, "fer_sample": fer},
+            "config": {"workload": workload_name(w), "sample": desc, "fer_sample": fer},
             "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -271,14 +273,14 @@ def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
 
     torch.cuda.set_device(local_rank)
     ps.load(build_if_missing=True)
-    w = dict(WORKLOAD)
+    w = dict(WORKLOAD, systematic=bool(args.systematic))
     if args.frames:
         w["frames"] = int(args.frames)
     B, N, K, crc, D, L = w["frames"], w["N"], w["K"], w["crc"], w["D"], w["L"]
     kmsg = K - crc
     npts = len(w["ebn0"])
     fr = ps.polar_construct(N, K, w["design_snr_db"])
-    plan = ps.Plan(N, K, fr, fast_nodes=w["fast"], crc=crc)
+    plan = ps.Plan(N, K, fr, fast_nodes=w["fast"], crc=crc, systematic=w["systematic"])
     llrs, d_msg = make_gpu_inputs(ps, plan, B, rank, w)
     outs = [(torch.empty((B, plan.msg_words), dtype=torch.int32, device="cuda"),
              torch.empty(B, dtype=torch.float32, device="cuda"), torch.empty(B, dtype=torch.int8, device="cuda"))
@@ -371,7 +373,7 @@ def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
         e2e = bench_e2e(ps, plan, llrs, w, args, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_frames)
+        cpu = cpu_baseline(args.cpu_frames, w)
     clocks = sampler.summary() if sampler else None
 
     if rank == 0:
@@ -786,12 +788,12 @@ def bench_serve(args, rank: int, world: int, local_rank: int) -> None:
         print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(frames: int):
+def cpu_baseline(frames: int, w=WORKLOAD):
     import os as _os
 
     threads = _os.cpu_count() or 1
-    fr, msg, llrs = oracle_sample_inputs(frames, 0)
-    dt, _ = run_oracle(fr, llrs, threads)
+    fr, msg, llrs = oracle_sample_inputs(frames, 0, w)
+    dt, _ = run_oracle(fr, llrs, threads, w)
     kmsg = WORKLOAD["K"] - WORKLOAD["crc"]
     nf = frames * len(llrs)
     return {"value": nf * kmsg / dt / 1e9, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
@@ -816,6 +818,7 @@ def main(argv=None) -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lpt", action="store_true", help="mixed workload: claim frames in batch order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--systematic", action="store_true", help="sweep: systematic encoding and decoding")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -93,6 +93,20 @@ int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_nodes, int c
  * Errors: POLAR_EINVAL (NULL plan, non-finite scale), POLAR_ECUDA. */
 int polar_plan_set_scales(polar_plan *plan, const float *scales);
 
+/* Systematic encoding (Sec. 2.2.2, Sec. 4): with on != 0 the codeword
+ * itself carries the K information bits (message, then CRC) on the
+ * information set, x_A = info with u frozen = 0, and decoders read the
+ * message straight from the decoded codeword (no re-encode); on = 0 restores
+ * the non-systematic code.  The encoder computes x as two passes of the XOR
+ * tree with the frozen positions cleared in between, which is systematic
+ * exactly when the information set is closed under the bit-subset order
+ * between its members (true of the constructions this library makes); a set
+ * for which the two passes are not systematic is rejected.  Host only; call
+ * before the plan's first GPU use (its device tables are made then).
+ * Errors: POLAR_EINVAL (NULL plan, plan already on a device, unsupported
+ * information set), POLAR_ENOMEM. */
+int polar_plan_set_systematic(polar_plan *plan, int on);
+
 /* Release a plan and its device copy (synchronous; no call using it may be
  * in flight).  NULL is ignored. */
 void polar_plan_destroy(polar_plan *plan);
@@ -104,7 +118,8 @@ void polar_plan_destroy(polar_plan *plan);
  * 7 = information leaf.  Returns the number of operations, or < 0. */
 int polar_plan_schedule(const polar_plan *plan, int32_t *ops_out, int max_ops);
 
-/* Encode B messages on the GPU (Sec. 2.1; the CRC of the plan is appended).
+/* Encode B messages on the GPU (Sec. 2.1; the CRC of the plan is appended;
+ * systematic when the plan is, see polar_plan_set_systematic).
  * d_msg: device, [B, ceil((K-crc)/32)] packed message bits.  d_codeword:
  * device, [B, ceil(N/32)] packed codeword bits.  Asynchronous on stream. */
 int polar_encode_batch(const polar_plan *plan, const uint32_t *d_msg, int B, uint32_t *d_codeword, void *stream);

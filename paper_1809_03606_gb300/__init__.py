@@ -28,7 +28,7 @@ EXPORTED = (
     "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info", "scs_decode_batch_noalloc",
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
     "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64", "polar_plan_set_scales", "polar_mixed_order",
-    "polar_serve", "polar_serve_baseline",
+    "polar_serve", "polar_serve_baseline", "polar_plan_set_systematic",
 )
 
 _lock = threading.Lock()
@@ -66,6 +66,7 @@ def load(build_if_missing: bool = False):
         lib.polar_plan_destroy.restype = None
         lib.polar_plan_schedule.argtypes = [vp, vp, i32]
         lib.polar_plan_set_scales.argtypes = [vp, vp]
+        lib.polar_plan_set_systematic.argtypes = [vp, i32]
         lib.polar_encode_batch.argtypes = [vp, vp, i32, vp, vp]
         lib.polar_encode.argtypes = [vp, i32, i32, vp, i32, vp]
         lib.scs_decode_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
@@ -128,13 +129,17 @@ def polar_construct(N: int, K: int, design_snr_db: float) -> np.ndarray:
 class Plan:
     """Owner of a ``polar_plan*`` (the schedule of Fig. fsscsch plus tables)."""
 
-    def __init__(self, N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0):
+    def __init__(self, N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0,
+                 systematic: bool = False):
         fr = np.ascontiguousarray(frozen, dtype=np.uint8)
         if fr.size != N:
             raise ValueError("frozen mask must have N entries")
         h = C.c_void_p()
         _check("polar_plan_create", load().polar_plan_create(N, K, _np_ptr(fr), int(bool(fast_nodes)), crc, C.byref(h)))
         self._h = h
+        self.systematic = False
+        if systematic:
+            polar_plan_set_systematic(self, True)
         self.N, self.K, self.crc, self.fast = N, K, crc, bool(fast_nodes)
         self.kmsg = K - crc
         self.frozen = fr.copy()
@@ -164,8 +169,15 @@ class Plan:
             pass
 
 
-def polar_plan_create(N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0) -> Plan:
-    return Plan(N, K, frozen, fast_nodes, crc)
+def polar_plan_create(N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0,
+                      systematic: bool = False) -> Plan:
+    return Plan(N, K, frozen, fast_nodes, crc, systematic)
+
+
+def polar_plan_set_systematic(plan: Plan, on: bool) -> None:
+    """Systematic encoding and decoding for the plan (before its first GPU use)."""
+    _check("polar_plan_set_systematic", load().polar_plan_set_systematic(plan.handle, int(bool(on))))
+    plan.systematic = bool(on)
 
 
 def polar_plan_destroy(plan: Plan) -> None:

@@ -68,6 +68,7 @@ static void free_tables(DeviceTables &d) {
     cudaFree(d.info_pos);
     cudaFree(d.crc_contrib);
     cudaFree(d.info_mask);
+    cudaFree(d.info_bits);
     cudaFree(d.scales);
     d = DeviceTables{};
 }
@@ -90,6 +91,7 @@ int plan_device(const polar_plan *p, const DeviceTables **out) {
     if (e == cudaSuccess) e = upload(&d.info_pos, p->info_pos);
     if (e == cudaSuccess) e = upload(&d.crc_contrib, p->crc_contrib);
     if (e == cudaSuccess) e = upload(&d.info_mask, p->info_mask);
+    if (e == cudaSuccess) e = upload(&d.info_bits, p->info_bits);
     if (e == cudaSuccess) e = upload(&d.scales, p->scales);
     if (e != cudaSuccess) {
         free_tables(d);

@@ -1,5 +1,7 @@
 // encode.cu - batched polar encoding c = u F^{(x)n} (Sec. 2.1, Fig. encoder)
-// with the CRC of the plan appended to the message.
+// with the CRC of the plan appended to the message; systematic codes
+// (Sec. 2.2.2) take a second pass of the XOR tree after the frozen
+// positions of the first pass's output are cleared.
 //
 // One warp per frame: the message bits are scattered onto the information
 // set in a packed shared-memory row, the CRC register is the XOR of the
@@ -23,7 +25,30 @@ struct EncArgs {
     int B, N, W, Kmsg, crc, msg_words;
     const uint16_t *info_pos;
     const uint32_t *crc_contrib;
+    const uint32_t *info_bits;  // W words, information positions (systematic pass)
+    int systematic;
 };
+
+// u <- u F^{(x)n} on the warp's packed row: shift/mask stages inside words,
+// word XORs across words
+__device__ void xor_tree(uint32_t *u, int N, int W, int lane) {
+    for (int k = lane; k < W; k += 32) {
+        uint32_t x = u[k];
+        if (N > 1) x ^= (x >> 1) & 0x55555555u;
+        if (N > 2) x ^= (x >> 2) & 0x33333333u;
+        if (N > 4) x ^= (x >> 4) & 0x0F0F0F0Fu;
+        if (N > 8) x ^= (x >> 8) & 0x00FF00FFu;
+        if (N > 16) x ^= (x >> 16) & 0x0000FFFFu;
+        if (N < 32) x &= (1u << N) - 1u;
+        u[k] = x;
+    }
+    __syncwarp();
+    for (int hw = 1; hw < W; hw <<= 1) {
+        for (int k = lane; k < W; k += 32)
+            if (!(k & hw)) u[k] ^= u[k + hw];
+        __syncwarp();
+    }
+}
 
 __global__ void __launch_bounds__(128) polar_encode_kernel(EncArgs a) {
     extern __shared__ uint32_t esm[];
@@ -53,21 +78,11 @@ __global__ void __launch_bounds__(128) polar_encode_kernel(EncArgs a) {
             }
         }
         __syncwarp();
-        for (int k = lane; k < a.W; k += 32) {
-            uint32_t x = u[k];
-            if (a.N > 1) x ^= (x >> 1) & 0x55555555u;
-            if (a.N > 2) x ^= (x >> 2) & 0x33333333u;
-            if (a.N > 4) x ^= (x >> 4) & 0x0F0F0F0Fu;
-            if (a.N > 8) x ^= (x >> 8) & 0x00FF00FFu;
-            if (a.N > 16) x ^= (x >> 16) & 0x0000FFFFu;
-            if (a.N < 32) x &= (1u << a.N) - 1u;
-            u[k] = x;
-        }
-        __syncwarp();
-        for (int hw = 1; hw < a.W; hw <<= 1) {
-            for (int k = lane; k < a.W; k += 32)
-                if (!(k & hw)) u[k] ^= u[k + hw];
+        xor_tree(u, a.N, a.W, lane);
+        if (a.systematic) {
+            for (int k = lane; k < a.W; k += 32) u[k] &= __ldg(a.info_bits + k);
             __syncwarp();
+            xor_tree(u, a.N, a.W, lane);
         }
         uint32_t *c = a.cw + size_t(b) * a.W;
         for (int k = lane; k < a.W; k += 32) c[k] = u[k];
@@ -80,7 +95,8 @@ __global__ void __launch_bounds__(128) polar_encode_kernel(EncArgs a) {
 int launch_polar_encode(const polar_plan *p, const DeviceTables *dt, const uint32_t *d_msg, int B, uint32_t *d_cw,
                         cudaStream_t stream) {
     if (B == 0) return 0;
-    EncArgs a{d_msg, d_cw, B, p->N, p->W, p->Kmsg, p->crc, (p->Kmsg + 31) / 32, dt->info_pos, dt->crc_contrib};
+    EncArgs a{d_msg, d_cw, B, p->N, p->W, p->Kmsg, p->crc, (p->Kmsg + 31) / 32, dt->info_pos, dt->crc_contrib,
+              dt->info_bits, p->systematic};
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);

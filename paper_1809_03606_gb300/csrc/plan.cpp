@@ -168,7 +168,11 @@ extern "C" int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_n
             if (!p->frozen[size_t(i)]) p->info_pos.push_back(uint16_t(i));
         p->msg_pos.assign(p->info_pos.begin(), p->info_pos.begin() + p->Kmsg);
         p->info_mask.assign(size_t(N), 0u);
-        for (int i = 0; i < N; ++i) p->info_mask[size_t(i)] = p->frozen[size_t(i)] ? 0u : 1u;
+        p->info_bits.assign(size_t(p->W), 0u);
+        for (int i = 0; i < N; ++i) {
+            p->info_mask[size_t(i)] = p->frozen[size_t(i)] ? 0u : 1u;
+            if (!p->frozen[size_t(i)]) p->info_bits[size_t(i >> 5)] |= 1u << (i & 31);
+        }
 
         // CRC register of each unit message (linearity of the long division)
         if (crc) {
@@ -183,31 +187,98 @@ extern "C" int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_n
                 reg = (reg << 1) & mask;
                 if (fb) reg ^= poly;
             }
-            // syndrome rows over codeword bits: codeword bit q contributes
-            // through u_j for every j whose bits are a subset of q's
-            // (u = x F^{(x)n} since F^{(x)n} is an involution)
-            std::vector<int> info_rank(size_t(N), -1);
-            for (int k = 0; k < K; ++k) info_rank[p->info_pos[size_t(k)]] = k;
-            p->crc_rows.assign(size_t(crc) * size_t(p->W), 0u);
-            for (int q = 0; q < N; ++q) {
-                uint32_t syn = 0;
-                for (int j = q;; j = (j - 1) & q) {  // all submasks of q
-                    const int k = info_rank[size_t(j)];
-                    if (k >= 0) {
-                        if (k < p->Kmsg) syn ^= p->crc_contrib[size_t(k)];
-                        else syn ^= 1u << (crc - 1 - (k - p->Kmsg));
-                    }
-                    if (j == 0) break;
-                }
-                for (int r = 0; r < crc; ++r)
-                    if ((syn >> r) & 1u) p->crc_rows[size_t(r) * size_t(p->W) + size_t(q >> 5)] |= 1u << (q & 31);
-            }
+            build_crc_rows(p);
         }
     } catch (...) {
         delete p;
         return POLAR_ENOMEM;
     }
     *out = p;
+    return 0;
+}
+
+namespace polarscs {
+
+// Syndrome rows over codeword bits.  Non-systematic: codeword bit q reaches
+// u_j for every j whose bits are a subset of q's (u = x F^{(x)n}, an
+// involution), and u_j on the information set is message bit rank(j).
+// Systematic: information bit k is codeword bit info_pos[k] itself.
+void build_crc_rows(polar_plan *p) {
+    const int N = p->N, K = p->K, crc = p->crc;
+    p->crc_rows.assign(size_t(crc) * size_t(p->W), 0u);
+    if (!crc) return;
+    std::vector<int> info_rank(size_t(N), -1);
+    for (int k = 0; k < K; ++k) info_rank[p->info_pos[size_t(k)]] = k;
+    auto unit = [&](int k) -> uint32_t {  // syndrome of information bit k alone
+        return k < p->Kmsg ? p->crc_contrib[size_t(k)] : (1u << (crc - 1 - (k - p->Kmsg)));
+    };
+    for (int q = 0; q < N; ++q) {
+        uint32_t syn = 0;
+        if (p->systematic) {
+            if (info_rank[size_t(q)] >= 0) syn = unit(info_rank[size_t(q)]);
+        } else {
+            for (int j = q;; j = (j - 1) & q) {  // all submasks of q
+                const int k = info_rank[size_t(j)];
+                if (k >= 0) syn ^= unit(k);
+                if (j == 0) break;
+            }
+        }
+        for (int r = 0; r < crc; ++r)
+            if ((syn >> r) & 1u) p->crc_rows[size_t(r) * size_t(p->W) + size_t(q >> 5)] |= 1u << (q & 31);
+    }
+}
+
+namespace {
+
+// x <- x F^{(x)n} on a packed N-bit row (the XOR tree of Sec. 2.1)
+void xor_tree(std::vector<uint64_t> &w, int N) {
+    static const uint64_t lo[6] = {0x5555555555555555ull, 0x3333333333333333ull, 0x0F0F0F0F0F0F0F0Full,
+                                   0x00FF00FF00FF00FFull, 0x0000FFFF0000FFFFull, 0x00000000FFFFFFFFull};
+    for (int st = 0; (1 << st) < N && st < 6; ++st)
+        for (auto &x : w) x ^= (x >> (1 << st)) & lo[st];
+    const int nw = int(w.size());
+    for (int h = 1; h < nw; h <<= 1)
+        for (int k = 0; k < nw; ++k)
+            if (!(k & h)) w[size_t(k)] ^= w[size_t(k + h)];
+}
+
+// the two-pass encoder (x = F(clear_frozen(F(v))), v the information bits
+// placed on A) is systematic iff it maps every unit information vector to
+// itself on A; both passes are linear, so unit vectors suffice
+bool two_pass_is_systematic(const polar_plan *p) {
+    const int N = p->N, nw = (N + 63) / 64;
+    std::vector<uint64_t> mask(static_cast<size_t>(nw), 0ull), w(static_cast<size_t>(nw), 0ull);
+    for (int i = 0; i < N; ++i)
+        if (!p->frozen[size_t(i)]) mask[size_t(i >> 6)] |= 1ull << (i & 63);
+    for (int k = 0; k < p->K; ++k) {
+        const int a = p->info_pos[size_t(k)];
+        std::fill(w.begin(), w.end(), 0ull);
+        w[size_t(a >> 6)] = 1ull << (a & 63);
+        xor_tree(w, N);
+        for (int q = 0; q < nw; ++q) w[size_t(q)] &= mask[size_t(q)];
+        xor_tree(w, N);
+        for (int q = 0; q < nw; ++q) {
+            const uint64_t want = (q == (a >> 6)) ? (1ull << (a & 63)) : 0ull;
+            if ((w[size_t(q)] & mask[size_t(q)]) != want) return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace
+}  // namespace polarscs
+
+extern "C" int polar_plan_set_systematic(polar_plan *p, int on) {
+    if (!p) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(p->mu);
+    if (p->dev.device >= 0) return POLAR_EINVAL;  // tables already on a device
+    try {
+        if (on && !polarscs::two_pass_is_systematic(p)) return POLAR_EINVAL;
+        p->systematic = on ? 1 : 0;
+        polarscs::build_crc_rows(p);
+    } catch (...) {
+        return POLAR_ENOMEM;
+    }
     return 0;
 }
 

@@ -46,6 +46,7 @@ struct DeviceTables {
     uint16_t *info_pos = nullptr;    // K information indices
     uint32_t *crc_contrib = nullptr; // Kmsg CRC registers of unit messages
     uint8_t *info_mask = nullptr;    // N bytes: 1 = information leaf
+    uint32_t *info_bits = nullptr;   // W words: information positions, packed
     float *scales = nullptr;         // n per-stage f scales, or null (unscaled)
 };
 
@@ -62,6 +63,8 @@ struct polar_plan {
     std::vector<uint32_t> crc_contrib;
     std::vector<uint8_t> info_mask;
     std::vector<float> scales;  // empty: unscaled min-sum
+    std::vector<uint32_t> info_bits;  // W words: 1 = information position
+    int systematic = 0;               // codeword carries the information bits
     mutable std::mutex mu;
     mutable polarscs::DeviceTables dev;
 };
@@ -80,6 +83,9 @@ struct polar_plan_set {
 namespace polarscs {
 
 int validate_code(int N, int K, const uint8_t *frozen, int crc);
+// CRC syndrome rows over codeword bits for the plan's encoding (needs
+// info_pos, crc_contrib).
+void build_crc_rows(polar_plan *p);
 uint32_t crc_polynomial(int crc);
 // Upload the plan's tables to the current device (once).  Returns 0 or an error.
 int plan_device(const polar_plan *plan, const DeviceTables **out);

@@ -61,6 +61,7 @@ struct Code {
     const float *scales;  // per-stage factors on f outputs, or null
     int N, n, W, Kmsg, crc, nops, nbranch, info_words;
     int snap_words;  // words per snapshot slot: W beta words + 4 meta words, padded
+    int systematic;  // message bits read straight from the codeword estimate
 };
 
 constexpr int kMaxCodes = 64;  // codes of one mixed batch (shared-memory table)
@@ -555,25 +556,28 @@ __device__ __noinline__ bool crc_ok(const Code &c, const uint32_t *beta, int lan
 }
 
 // output: re-encode the codeword estimate (F is an involution, Sec. 2.2.2)
-// and read the message bits off the information set
+// and read the message bits off the information set; a systematic code
+// carries them in the codeword estimate itself
 __device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *orow, int lane) {
     const int W = c.W, N = c.N;
-    #pragma unroll 1
-    for (int k = lane; k < W; k += 32) {
-        uint32_t x = u[k];
-        if (N > 1) x ^= (x >> 1) & 0x55555555u;
-        if (N > 2) x ^= (x >> 2) & 0x33333333u;
-        if (N > 4) x ^= (x >> 4) & 0x0F0F0F0Fu;
-        if (N > 8) x ^= (x >> 8) & 0x00FF00FFu;
-        if (N > 16) x ^= (x >> 16) & 0x0000FFFFu;
-        u[k] = x;
-    }
-    __syncwarp();
-    for (int hw = 1; hw < W; hw <<= 1) {
+    if (!c.systematic) {
         #pragma unroll 1
-        for (int k = lane; k < W; k += 32)
-            if (!(k & hw)) u[k] ^= u[k + hw];
+        for (int k = lane; k < W; k += 32) {
+            uint32_t x = u[k];
+            if (N > 1) x ^= (x >> 1) & 0x55555555u;
+            if (N > 2) x ^= (x >> 2) & 0x33333333u;
+            if (N > 4) x ^= (x >> 4) & 0x0F0F0F0Fu;
+            if (N > 8) x ^= (x >> 8) & 0x00FF00FFu;
+            if (N > 16) x ^= (x >> 16) & 0x0000FFFFu;
+            u[k] = x;
+        }
         __syncwarp();
+        for (int hw = 1; hw < W; hw <<= 1) {
+            #pragma unroll 1
+            for (int k = lane; k < W; k += 32)
+                if (!(k & hw)) u[k] ^= u[k + hw];
+            __syncwarp();
+        }
     }
     #pragma unroll 1
     for (int ow = lane; ow < c.info_words; ow += 32) {
@@ -1032,7 +1036,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         for (int k = lane; k < W; k += 32) w.beta[k] = 0u;
     }
     __syncwarp();
-    ops += uint32_t(n) * uint32_t(W);
+    if (!c.systematic) ops += uint32_t(n) * uint32_t(W);
     write_output(c, w.beta, orow, lane);
     if (lane == 0) {
         if (status == POLAR_TIMEOUT) out_pm = __int_as_float(0x7f800000);
@@ -1197,6 +1201,7 @@ Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, co
     c.nbranch = p->nbranch;
     c.info_words = (p->Kmsg + 31) / 32;
     c.snap_words = ((p->W + 4) + 7) & ~7;
+    c.systematic = p->systematic;
     return c;
 }
 

@@ -116,3 +116,28 @@ def test_bit_packing_round_trip():
         assert np.array_equal(ps.unpack_bits(w, k), bits)
     w = ps.pack_bits(np.array([[1, 0, 1] + [0] * 29 + [1]], np.uint8))
     assert w.view(np.uint32)[0, 0] == 0b101 and w.view(np.uint32)[0, 1] == 1
+
+
+def test_set_systematic_host_checks(lib):
+    """polar_plan_set_systematic: the two-pass encoder check and argument checks
+    (host logic only; nothing touches a device)."""
+    N, K = 1024, 512
+    fr = ps.polar_construct(N, K, 0.0)
+    plan = ps.Plan(N, K, fr, fast_nodes=True, crc=16, systematic=True)
+    assert plan.systematic
+    ps.polar_plan_set_systematic(plan, False)
+    assert not plan.systematic
+    assert lib.polar_plan_set_systematic(None, 1) == ps.POLAR_EINVAL
+    # information set {1, 3, 7} of N = 8: three members lie between 1 and 7
+    # in the bit-subset order, so two passes of the XOR tree are not systematic
+    fr8 = np.ones(8, np.uint8)
+    fr8[[1, 3, 7]] = 0
+    p8 = ps.Plan(8, 3, fr8, fast_nodes=False)
+    assert lib.polar_plan_set_systematic(p8.handle, 1) == ps.POLAR_EINVAL
+    assert lib.polar_plan_set_systematic(p8.handle, 0) == 0
+    # {1, 7}: two members between 1 and 7 (an even number), so two passes
+    # are systematic although 3 and 5 are frozen
+    fr8 = np.ones(8, np.uint8)
+    fr8[[1, 7]] = 0
+    p8b = ps.Plan(8, 2, fr8, fast_nodes=False)
+    assert lib.polar_plan_set_systematic(p8b.handle, 1) == 0

@@ -20,6 +20,10 @@ def _frozen_sets(N):
     import oracle
 
     sets = [oracle.construct(N, K, snr) for K in (1, N // 4, N // 2, 3 * N // 4, N - 1) for snr in (0.0, 3.0)]
+    for info in ([1, 3, 7], [1, 7], [2, 4, 6, 7], [0, 5]):  # sets not closed under the bit-subset order
+        fr = np.ones(N, np.uint8)
+        fr[info] = 0
+        sets.append(fr)
     return sets
 
 
