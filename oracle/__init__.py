@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "polar_oracle.c")
+_INC = os.path.join(_HERE, "polar_oracle_exact.inc")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -36,7 +37,8 @@ _FLAGS = ["-O2", "-fno-fast-math", "-ffp-contract=off", "-std=c11", "-shared", "
 def build(force: bool = False) -> str:
     """Compile the oracle for this host (gcc, no architecture-specific flags)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_INC))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.run(["gcc", *_FLAGS, "-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
@@ -65,6 +67,7 @@ def _load():
             lib.or_scs_decode_sx.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, C.c_int, u8p, f32p, u8p, u64p]
             lib.or_scs_decode_batch_sx.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, C.c_int, u8p, f32p, i8p, u64p]
             lib.or_scs_decode_exact.argtypes = [f64p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, u8p, f64p]
+            lib.or_scs_decode_exact_f32.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, u8p, f32p]
             lib.or_gsc_forward.argtypes = [f64p, u8p, C.c_int, f64p, f64p]
             lib.or_gsc_loss_grad.argtypes = [f64p, u8p, C.c_int, C.c_int, u8p, f64p, f64p, f64p]
             _lib = lib
@@ -213,16 +216,27 @@ def scs_decode_batch(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fas
     return msg, pm, status, stats
 
 
-def scs_decode_exact(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, D: int, L: int):
-    """Double-precision exact-f bit-level SCS (N <= 64).  Returns (status, codeword, pm)."""
-    llr = np.ascontiguousarray(llr, dtype=np.float64)
+def scs_decode_exact(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, D: int, L: int,
+                     precision: str = "f64"):
+    """Exact-f bit-level SCS without CRC, in double (``f64``) or float
+    (``f32``).  Returns (status, codeword, pm)."""
     fr = _u8(frozen)
     cw = np.zeros(N, np.uint8)
-    pm = C.c_double(0.0)
-    rc = _load().or_scs_decode_exact(_p(llr, C.c_double), N, K, _p(fr, C.c_uint8), D, L, _p(cw, C.c_uint8), C.byref(pm))
+    if precision == "f64":
+        llr = np.ascontiguousarray(llr, dtype=np.float64)
+        pm = C.c_double(0.0)
+        rc = _load().or_scs_decode_exact(_p(llr, C.c_double), N, K, _p(fr, C.c_uint8), D, L, _p(cw, C.c_uint8),
+                                         C.byref(pm))
+    elif precision == "f32":
+        llr = np.ascontiguousarray(llr, dtype=np.float32)
+        pm = C.c_float(0.0)
+        rc = _load().or_scs_decode_exact_f32(_p(llr, C.c_float), N, K, _p(fr, C.c_uint8), D, L, _p(cw, C.c_uint8),
+                                             C.byref(pm))
+    else:
+        raise ValueError("precision is 'f64' or 'f32'")
     if rc < 0:
         raise ValueError(f"or_scs_decode_exact -> {rc}")
-    return rc, cw, float(pm.value)
+    return rc, cw, (float(pm.value) if precision == "f64" else np.float32(pm.value))
 
 
 def gsc_forward(llr: np.ndarray, u: np.ndarray, scale: np.ndarray) -> np.ndarray:

@@ -833,143 +833,37 @@ int or_scs_decode_batch(const float *llr, int B, int N, int K, const uint8_t *fr
 }
 
 /* ------------------------------------------------------------------------ */
-/* Exact-f variant in double precision, bit-level (no fast nodes): the      */
-/* f of the box-plus rule 2 atanh(tanh(a/2) tanh(b/2)) and the leaf metric  */
-/* PM += ln(1 + exp(-(1 - 2u) alpha)).  Used to pin the search to maximum   */
-/* likelihood on tiny codes.                                                */
+/* Exact-f variant, bit-level (no fast nodes): the f of the box-plus rule   */
+/* and the exact leaf metric ln(1 + exp(-(1 - 2u) alpha)); in double it     */
+/* pins the search to maximum likelihood on tiny codes, in float it is the  */
+/* reference of the GPU's exact-f decoder (decisions in the paper's FP32).  */
 /* ------------------------------------------------------------------------ */
-static double softplus(double x) { return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
-
-static double f_exact(double a, double b) {
-    /* 2 atanh(tanh(a/2) tanh(b/2)) = sgn(a)sgn(b)min(|a|,|b|) + ln(1+e^-|a+b|) - ln(1+e^-|a-b|) */
-    double m = fabs(a) < fabs(b) ? fabs(a) : fabs(b);
-    double s = ((a < 0) != (b < 0)) ? -m : m;
-    return s + log1p(exp(-fabs(a + b))) - log1p(exp(-fabs(a - b)));
-}
-
-/* bit-level SC tree quantities computed directly from u_0^{i-1}: the alpha of leaf i */
-static double ex_leaf_alpha(const double *llr, const uint8_t *u, int N, int i) {
-    /* recursive definition of Eq. llrcalc on the subtree containing leaf i */
-    if (N == 1) return llr[0];
-    int h = N / 2;
-    double *a = (double *)malloc(sizeof(double) * h);
-    double r;
-    if (i < h) {
-        for (int k = 0; k < h; k++) a[k] = f_exact(llr[k], llr[k + h]);
-        r = ex_leaf_alpha(a, u, h, i);
-    } else {
-        /* beta of the left half = encoding of u_0^{h-1} */
-        uint8_t *x = (uint8_t *)malloc(h);
-        or_encode(u, h, x);
-        for (int k = 0; k < h; k++) a[k] = x[k] ? llr[k + h] - llr[k] : llr[k + h] + llr[k];
-        free(x);
-        r = ex_leaf_alpha(a, u + h, h, i - h);
-    }
-    free(a);
-    return r;
-}
+#define X(name) name##_f64
+#define REAL double
+#define LOG1P log1p
+#define EXP exp
+#define FABS fabs
+#include "polar_oracle_exact.inc"
+#undef X
+#undef REAL
+#undef LOG1P
+#undef EXP
+#undef FABS
+#define X(name) name##_f32
+#define REAL float
+#define LOG1P log1pf
+#define EXP expf
+#define FABS fabsf
+#include "polar_oracle_exact.inc"
+#undef X
+#undef REAL
+#undef LOG1P
+#undef EXP
+#undef FABS
 
 int or_scs_decode_exact(const double *llr, int N, int K, const uint8_t *frozen, int D, int L, uint8_t *cw_out,
                         double *pm_out) {
-    /* bit-level stack search over the leaves with exact LLRs; path state is */
-    /* the bit vector u_0^{len-1}; alpha is recomputed from the root.        */
-    if (!is_pow2(N) || N > 64 || K < 1 || K > N || D < 1 || L < 1) return OR_EINVAL;
-    typedef struct {
-        double pm;
-        int len, done;
-        uint32_t seq;
-        uint8_t u[64];
-    } ent;
-    ent *st = (ent *)malloc(sizeof(ent) * D);
-    uint8_t *valid = (uint8_t *)calloc(D, 1);
-    int *cnt = (int *)calloc(N + 1, sizeof(int));
-    if (!st || !valid || !cnt) {
-        free(st);
-        free(valid);
-        free(cnt);
-        return OR_ENOMEM;
-    }
-    int ns = 1;
-    uint32_t seq_next = 1;
-    memset(&st[0], 0, sizeof(ent));
-    valid[0] = 1;
-    int rc = OR_CRC_FAIL;
-    *pm_out = INFINITY;
-    while (ns > 0) {
-        int j = -1;
-        for (int q = 0; q < D; q++)
-            if (valid[q] && (j < 0 || st[q].pm < st[j].pm || (st[q].pm == st[j].pm && st[q].seq > st[j].seq))) j = q;
-        ent p = st[j];
-        valid[j] = 0;
-        ns--;
-        if (p.done) { /* complete path popped: it is the best one */
-            or_encode(p.u, N, cw_out);
-            *pm_out = p.pm;
-            rc = OR_OK;
-            break;
-        }
-        /* extend through frozen leaves */
-        while (p.len < N && frozen[p.len]) {
-            double a = ex_leaf_alpha(llr, p.u, N, p.len);
-            p.u[p.len] = 0;
-            p.pm = p.pm + softplus(-a);
-            p.len++;
-        }
-        ent c[2];
-        int nc;
-        if (p.len == N) { /* completed: compete again on the stack */
-            c[0] = p;
-            c[0].done = 1;
-            c[0].seq = seq_next;
-            nc = 1;
-        } else {
-            int s = p.len;
-            if (++cnt[s] >= L)
-                for (int q = 0; q < D; q++)
-                    if (valid[q] && st[q].len <= s) {
-                        valid[q] = 0;
-                        ns--;
-                    }
-            double a = ex_leaf_alpha(llr, p.u, N, s);
-            int h = a < 0.0;
-            for (int k = 0; k < 2; k++) {
-                int bit = k == 0 ? h : 1 - h;
-                c[k] = p;
-                c[k].u[s] = (uint8_t)bit;
-                c[k].pm = p.pm + softplus(-(1.0 - 2.0 * bit) * a);
-                c[k].len = s + 1;
-                c[k].seq = seq_next + (uint32_t)(1 - k);
-            }
-            nc = 2;
-        }
-        seq_next += (uint32_t)nc;
-        for (int k = 0; k < nc; k++) {
-            int slot = -1;
-            if (ns < D) {
-                for (int q = 0; q < D; q++)
-                    if (!valid[q]) {
-                        slot = q;
-                        break;
-                    }
-                ns++;
-            } else {
-                int w = -1;
-                for (int q = 0; q < D; q++)
-                    if (valid[q] && (w < 0 || st[q].pm > st[w].pm || (st[q].pm == st[w].pm && st[q].seq < st[w].seq)))
-                        w = q;
-                if (c[k].pm < st[w].pm) slot = w;
-            }
-            if (slot >= 0) {
-                st[slot] = c[k];
-                valid[slot] = 1;
-            }
-        }
-    }
-    free(st);
-    free(valid);
-    free(cnt);
-    (void)K;
-    return rc;
+    return or_scs_decode_exact_f64(llr, N, K, frozen, D, L, cw_out, pm_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1056,7 +950,7 @@ int or_gsc_loss_grad(const double *llr, const uint8_t *u, int B, int N, const ui
         for (int i = 0; i < N; i++) {
             if (frozen[i]) continue;
             double sgn = 1.0 - 2.0 * ub[i], z = -sgn * tree[i];
-            loss += softplus(z) * norm;
+            loss += softplus_f64(z) * norm;
             /* d softplus(z)/dL = sigmoid(z) * (-sgn) */
             double sig = 1.0 / (1.0 + exp(-z));
             adj[i] = sig * (-sgn) * norm;
