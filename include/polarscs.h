@@ -107,6 +107,19 @@ int polar_plan_set_scales(polar_plan *plan, const float *scales);
  * information set), POLAR_ENOMEM. */
 int polar_plan_set_systematic(polar_plan *plan, int on);
 
+/* Exact-f decoding: with on != 0, scs_decode_batch(_noalloc) decodes the
+ * plan with the box-plus f of Eq. llrcalc itself, 2 atanh(tanh(a/2)
+ * tanh(b/2)) evaluated as sgn(a) sgn(b) min(|a|,|b|) + ln(1 + e^-|a+b|) -
+ * ln(1 + e^-|a-b|), and the exact leaf metric of Eq. PMupd, PM += ln(1 +
+ * exp(-(1 - 2u) alpha)) at every leaf, in float32, instead of min-sum.  The
+ * plan must be bit-level (fast_nodes = 0: the fast-node decoders of Sec.
+ * 2.2.2 are min-sum rules) and without scales; exact plans are decoded by the
+ * uniform decoder only (not in plan sets).  Host only; call before the plan's
+ * first GPU use.  Counters keep the min-sum counting convention.
+ * Errors: POLAR_EINVAL (NULL plan, fast nodes, scales set, plan already on a
+ * device). */
+int polar_plan_set_exact(polar_plan *plan, int on);
+
 /* Release a plan and its device copy (synchronous; no call using it may be
  * in flight).  NULL is ignored. */
 void polar_plan_destroy(polar_plan *plan);

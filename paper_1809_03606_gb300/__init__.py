@@ -28,7 +28,7 @@ EXPORTED = (
     "polar_encode", "scs_decode_batch", "scs_decode", "polar_device_info", "scs_decode_batch_noalloc",
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
     "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64", "polar_plan_set_scales", "polar_mixed_order",
-    "polar_serve", "polar_serve_baseline", "polar_plan_set_systematic",
+    "polar_serve", "polar_serve_baseline", "polar_plan_set_systematic", "polar_plan_set_exact",
 )
 
 _lock = threading.Lock()
@@ -67,6 +67,7 @@ def load(build_if_missing: bool = False):
         lib.polar_plan_schedule.argtypes = [vp, vp, i32]
         lib.polar_plan_set_scales.argtypes = [vp, vp]
         lib.polar_plan_set_systematic.argtypes = [vp, i32]
+        lib.polar_plan_set_exact.argtypes = [vp, i32]
         lib.polar_encode_batch.argtypes = [vp, vp, i32, vp, vp]
         lib.polar_encode.argtypes = [vp, i32, i32, vp, i32, vp]
         lib.scs_decode_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
@@ -130,7 +131,7 @@ class Plan:
     """Owner of a ``polar_plan*`` (the schedule of Fig. fsscsch plus tables)."""
 
     def __init__(self, N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0,
-                 systematic: bool = False):
+                 systematic: bool = False, exact: bool = False):
         fr = np.ascontiguousarray(frozen, dtype=np.uint8)
         if fr.size != N:
             raise ValueError("frozen mask must have N entries")
@@ -138,8 +139,11 @@ class Plan:
         _check("polar_plan_create", load().polar_plan_create(N, K, _np_ptr(fr), int(bool(fast_nodes)), crc, C.byref(h)))
         self._h = h
         self.systematic = False
+        self.exact = False
         if systematic:
             polar_plan_set_systematic(self, True)
+        if exact:
+            polar_plan_set_exact(self, True)
         self.N, self.K, self.crc, self.fast = N, K, crc, bool(fast_nodes)
         self.kmsg = K - crc
         self.frozen = fr.copy()
@@ -172,6 +176,12 @@ class Plan:
 def polar_plan_create(N: int, K: int, frozen: np.ndarray, fast_nodes: bool = True, crc: int = 0,
                       systematic: bool = False) -> Plan:
     return Plan(N, K, frozen, fast_nodes, crc, systematic)
+
+
+def polar_plan_set_exact(plan: Plan, on: bool) -> None:
+    """Exact-f decoding for a bit-level plan (before its first GPU use)."""
+    _check("polar_plan_set_exact", load().polar_plan_set_exact(plan.handle, int(bool(on))))
+    plan.exact = bool(on)
 
 
 def polar_plan_set_systematic(plan: Plan, on: bool) -> None:

@@ -121,6 +121,7 @@ extern "C" void polar_plan_destroy(polar_plan *p) {
 extern "C" int polar_plan_set_scales(polar_plan *p, const float *scales) {
     if (!p) return POLAR_EINVAL;
     std::lock_guard<std::mutex> g(p->mu);
+    if (scales && p->exact) return POLAR_EINVAL;  // scales are a min-sum form
     if (scales) {
         for (int i = 0; i < p->n; ++i)
             if (!(scales[i] == scales[i]) || scales[i] > 3.0e38f || scales[i] < -3.0e38f) return POLAR_EINVAL;
@@ -170,7 +171,7 @@ extern "C" int polar_plan_set_create(const polar_plan *const *plans, int nplans,
     if (!out || !plans || nplans < 1 || nplans > 64) return POLAR_EINVAL;
     *out = nullptr;
     for (int i = 0; i < nplans; ++i) {
-        if (!plans[i]) return POLAR_EINVAL;
+        if (!plans[i] || plans[i]->exact) return POLAR_EINVAL;
         if (plans[i]->N > POLAR_MAX_N_GPU) return POLAR_ELIMIT;
     }
     polar_plan_set *set = new (std::nothrow) polar_plan_set();

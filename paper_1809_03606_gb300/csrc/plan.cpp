@@ -268,6 +268,15 @@ bool two_pass_is_systematic(const polar_plan *p) {
 }  // namespace
 }  // namespace polarscs
 
+extern "C" int polar_plan_set_exact(polar_plan *p, int on) {
+    if (!p) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(p->mu);
+    if (p->dev.device >= 0) return POLAR_EINVAL;  // tables already on a device
+    if (on && (p->fast || !p->scales.empty())) return POLAR_EINVAL;
+    p->exact = on ? 1 : 0;
+    return 0;
+}
+
 extern "C" int polar_plan_set_systematic(polar_plan *p, int on) {
     if (!p) return POLAR_EINVAL;
     std::lock_guard<std::mutex> g(p->mu);

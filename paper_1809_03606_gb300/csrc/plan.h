@@ -65,6 +65,7 @@ struct polar_plan {
     std::vector<float> scales;  // empty: unscaled min-sum
     std::vector<uint32_t> info_bits;  // W words: 1 = information position
     int systematic = 0;               // codeword carries the information bits
+    int exact = 0;                    // exact-f decoding (box-plus f, exact leaf metric)
     mutable std::mutex mu;
     mutable polarscs::DeviceTables dev;
 };

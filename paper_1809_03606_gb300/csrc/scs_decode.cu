@@ -128,9 +128,25 @@ __device__ __forceinline__ float g_op(float a, float b, uint32_t bit) {
     return __fadd_rn(b, __uint_as_float(__float_as_uint(a) ^ (bit << 31)));
 }
 
+// ln(1 + e^x), written so that neither branch overflows
+__device__ __forceinline__ float softplus_f(float x) {
+    return x > 0.0f ? __fadd_rn(x, log1pf(expf(-x))) : log1pf(expf(x));
+}
+
+// the box-plus f of Eq. llrcalc itself, 2 atanh(tanh(a/2) tanh(b/2)), as
+// sgn(a) sgn(b) min(|a|,|b|) + ln(1 + e^-|a+b|) - ln(1 + e^-|a-b|), summed
+// left to right (exact-f decoding)
+__device__ __forceinline__ float f_exact(float a, float b) {
+    const float m = fminf(fabsf(a), fabsf(b));
+    const float s = ((a < 0.0f) != (b < 0.0f)) ? -m : m;
+    return __fsub_rn(__fadd_rn(s, log1pf(expf(-fabsf(__fadd_rn(a, b))))), log1pf(expf(-fabsf(__fsub_rn(a, b)))));
+}
+
 __device__ __forceinline__ float pen_transform(float x, int mode) {
-    // 0: x; 1: |x| where HD(x) = 1 (disagrees with 0); 2: |x| where HD(x) = 0
+    // 0: x; 1: |x| where HD(x) = 1 (disagrees with 0); 2: |x| where HD(x) = 0;
+    // 3: ln(1 + e^-x), the exact metric of a leaf decided 0
     if (mode == 0) return x;
+    if (mode == 3) return softplus_f(-x);
     const bool neg = x < 0.0f;
     return (mode == 1) == neg ? fabsf(x) : 0.0f;
 }
@@ -205,8 +221,11 @@ __device__ __noinline__ int restore_switch(const uint32_t *sp, uint32_t *beta, i
 
 // f and g from the channel LLRs (the root stage, in global memory), out of
 // line: vector loads when the rows are 16-byte aligned
-__device__ __noinline__ void f_root(const float *P, float *C, int len, float sv, int vec, int lane) {
-    if (vec && len >= 128) {
+__device__ __noinline__ void f_root(const float *P, float *C, int len, float sv, int vec, int exact, int lane) {
+    if (exact) {
+        #pragma unroll 1
+        for (int i = lane; i < len; i += 32) C[i] = f_exact(P[i], P[i + len]);
+    } else if (vec && len >= 128) {
         #pragma unroll 1
         for (int i = 4 * lane; i < len; i += 128) {
             const float4 x = *reinterpret_cast<const float4 *>(P + i);
@@ -296,19 +315,23 @@ struct Warp {
     __device__ const float *stage(int lam) const { return lam == n ? root : alpha + (1 << lam); }
 
     // alpha of the even child (lamc) from its parent (Eq. llrcalc, f); every
-    // f output is multiplied by the stage scale (1.0, an exact identity, for
-    // plain min-sum)
+    // min-sum f output is multiplied by the stage scale (1.0, an exact
+    // identity, for plain min-sum); EXACT: the box-plus f itself
+    template <bool EXACT>
     __device__ void op_f(int lamc) const {
         const int len = 1 << lamc;
         float *C = alpha + len;
         const float sv = scales ? __ldg(scales + lamc) : 1.0f;
         if (lamc + 1 == n) {
-            f_root(root, C, len, sv, llr_vec, lane);
+            f_root(root, C, len, sv, llr_vec, EXACT ? 1 : 0, lane);
             __syncwarp();
             return;
         }
         const float *P = alpha + 2 * len;
-        if (len >= 128) {
+        if (EXACT) {
+            #pragma unroll 1
+            for (int i = lane; i < len; i += 32) C[i] = f_exact(P[i], P[i + len]);
+        } else if (len >= 128) {
             #pragma unroll 1
             for (int i = 4 * lane; i < len; i += 128) {
                 const float4 x = *reinterpret_cast<const float4 *>(P + i);
@@ -699,7 +722,7 @@ __device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int
     __syncwarp();
 }
 
-template <int NS>
+template <int NS, bool EXACT>
 __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Warp &w,
                                              unsigned b, uint32_t *orow) {
     const int lane = w.lane;
@@ -911,7 +934,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
                 ++t;
             }
             if (code == OP_F) {
-                w.op_f(lam);
+                w.template op_f<EXACT>(lam);
                 if (sched) ops += 2u << lam;
                 PT(PH_FG)
             } else if (code == OP_G) {
@@ -923,7 +946,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
                 ops += (lam < 5) ? 1u : (1u << (lam - 5));
                 PT(PH_COMB)
             } else {  // Rate-0 node or frozen leaf: beta = 0, PM += sum HD(a)|a|
-                const float pen = w.node_sum(lam, 1);
+                const float pen = w.node_sum(lam, EXACT ? 3 : 1);
                 w.set_range(lam, s, 0u);
                 pm = __fadd_rn(pm, pen);
                 ops += (2u << lam) + 1u;
@@ -989,7 +1012,14 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
                 ops += 4u * uint32_t(len) + 3u;
             } else {  // information leaf, Rate-1 or SPC: hard decisions first
                 const uint32_t q = w.node_hd(lam, s);
-                if (code == OP_LEAF1) {
+                if (code == OP_LEAF1 && EXACT) {  // ln(1 + e^-|a|), ln(1 + e^|a|)
+                    const float aa = fabsf(w.stage(0)[0]);
+                    cd.nc = 2;
+                    cd.rep = true;
+                    cd.rep0 = softplus_f(-aa);
+                    cd.rep1 = softplus_f(aa);
+                    ops += 4u;
+                } else if (code == OP_LEAF1) {
                     cd.mag[0] = fabsf(w.stage(0)[0]);
                     cd.nc = 2;
                     cd.masks = LEAF1_MASKS;
@@ -1059,7 +1089,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
 // MIXED = false: every frame uses a.code, a.D, a.L and row b of the LLR and
 // message buffers.  MIXED = true: frame b has its own code, D and L
 // (a.frames[b]) and offsets into packed LLR and message buffers.
-template <bool MIXED, int NS>
+template <bool MIXED, int NS, bool EXACT = false>
 __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Code codes_s[MIXED ? kMaxCodes : 1];
@@ -1085,7 +1115,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const Code &c = a.code;
                 Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                        my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
-                decode_frame<NS>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
+                decode_frame<NS, EXACT>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
             } else {
                 const int4 fd = a.frames[b];
                 if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
@@ -1099,7 +1129,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const long long lo = a.llr_off[b];
                 Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
                        reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales};
-                decode_frame<NS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
+                decode_frame<NS, false>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
             }
         }
     }
@@ -1170,7 +1200,7 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
             __syncwarp();
             Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                    my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
-            decode_frame<NS>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
+            decode_frame<NS, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
         }
         if (lane == 0) {
             a.t_done[k] = global_ns();
@@ -1208,7 +1238,7 @@ Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, co
 int warp_smem_bytes(int N, int W, int nbranch) { return ((4 * N + 4 * W + nbranch) + 15) & ~15; }
 
 // block size and persistent grid for a kernel with `warp_smem` bytes per warp
-template <bool MIXED, int NS>
+template <bool MIXED, int NS, bool EXACT = false>
 int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int *smem_out) {
     int dev = 0, sms = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1220,10 +1250,10 @@ int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int
     while (wpb > 1 && wpb * warp_smem + static_smem > max_smem) wpb >>= 1;
     if (wpb * warp_smem + static_smem > max_smem) return POLAR_ELIMIT;
     const int smem = wpb * warp_smem;
-    e = cudaFuncSetAttribute(scs_decode_kernel<MIXED, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(scs_decode_kernel<MIXED, NS, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel<MIXED, NS>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel<MIXED, NS, EXACT>, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return POLAR_ELIMIT;
     long long grid = (long long)sms * per_sm;
@@ -1233,6 +1263,26 @@ int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int
     *wpb_out = wpb;
     *smem_out = smem;
     return 0;
+}
+
+// the uniform kernel for a plan: stack rows by D, exact-f or min-sum by plan
+int uniform_shape(const polar_plan *p, int warp_smem, int B, int D, int wpb, int *grid, int *wpb_out, int *smem) {
+    if (p->exact)
+        return D <= 32 ? launch_shape<false, 1, true>(warp_smem, B, wpb, grid, wpb_out, smem)
+                       : launch_shape<false, 2, true>(warp_smem, B, wpb, grid, wpb_out, smem);
+    return D <= 32 ? launch_shape<false, 1>(warp_smem, B, wpb, grid, wpb_out, smem)
+                   : launch_shape<false, 2>(warp_smem, B, wpb, grid, wpb_out, smem);
+}
+
+void launch_uniform(const polar_plan *p, int D, int grid, int wpb, int smem, cudaStream_t stream, const Args &a) {
+    const dim3 g(static_cast<unsigned>(grid)), b(static_cast<unsigned>(wpb * 32));
+    if (p->exact) {
+        if (D <= 32) scs_decode_kernel<false, 1, true><<<g, b, size_t(smem), stream>>>(a);
+        else scs_decode_kernel<false, 2, true><<<g, b, size_t(smem), stream>>>(a);
+    } else {
+        if (D <= 32) scs_decode_kernel<false, 1><<<g, b, size_t(smem), stream>>>(a);
+        else scs_decode_kernel<false, 2><<<g, b, size_t(smem), stream>>>(a);
+    }
 }
 
 int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *d_llr, int B, int D, int L,
@@ -1254,8 +1304,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
 
     int grid = 0, wpb = 0, smem = 0;
-    int rc = D <= 32 ? launch_shape<false, 1>(a.warp_smem, B, 4, &grid, &wpb, &smem)
-                     : launch_shape<false, 2>(a.warp_smem, B, 4, &grid, &wpb, &smem);
+    int rc = uniform_shape(p, a.warp_smem, B, D, 4, &grid, &wpb, &smem);
     if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1269,8 +1318,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
     e = cudaMemsetAsync(ws, 0, 64, stream);
     if (e == cudaSuccess) {
-        if (D <= 32) scs_decode_kernel<false, 1><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
-        else scs_decode_kernel<false, 2><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+        launch_uniform(p, D, grid, wpb, smem, stream, a);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(ws, stream);
@@ -1294,6 +1342,8 @@ static int set_device_codes(const polar_plan_set *set, const Code **out) {
         return 0;
     }
     if (set->device >= 0) return POLAR_EINVAL;  // a set serves one device
+    for (const polar_plan *p : set->plans)
+        if (p->exact) return POLAR_EINVAL;  // plan sets decode with min-sum only
     std::vector<Code> codes(set->plans.size());
     for (size_t i = 0; i < set->plans.size(); ++i) {
         const DeviceTables *dt = nullptr;
@@ -1569,8 +1619,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     int wpb = 4;
     while (wpb > 1 && size_t(wpb) > warps_fit) wpb >>= 1;
     int grid = 0, smem = 0;
-    rc = D <= 32 ? launch_shape<false, 1>(a.warp_smem, B, wpb, &grid, &wpb, &smem)
-                 : launch_shape<false, 2>(a.warp_smem, B, wpb, &grid, &wpb, &smem);
+    rc = uniform_shape(p, a.warp_smem, B, D, wpb, &grid, &wpb, &smem);
     if (rc) return rc;
     const long long fit = (long long)(warps_fit / size_t(wpb));
     if (fit < grid) grid = int(fit);
@@ -1588,8 +1637,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
         e = cudaMemcpyAsync(tab + sc_off, p->scales.data(), sc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    if (D <= 32) scs_decode_kernel<false, 1><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
-    else scs_decode_kernel<false, 2><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
+    launch_uniform(p, D, grid, wpb, smem, stream, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? 0 : cuda_status(e);
 }

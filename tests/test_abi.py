@@ -141,3 +141,22 @@ def test_set_systematic_host_checks(lib):
     fr8[[1, 7]] = 0
     p8b = ps.Plan(8, 2, fr8, fast_nodes=False)
     assert lib.polar_plan_set_systematic(p8b.handle, 1) == 0
+
+
+def test_set_exact_host_checks(lib):
+    """polar_plan_set_exact takes bit-level plans without scales only, and
+    plan sets refuse exact plans (host logic only)."""
+    fr = ps.polar_construct(256, 128, 0.0)
+    fast = ps.Plan(256, 128, fr, fast_nodes=True)
+    assert lib.polar_plan_set_exact(fast.handle, 1) == ps.POLAR_EINVAL
+    assert lib.polar_plan_set_exact(None, 1) == ps.POLAR_EINVAL
+    scaled = ps.Plan(256, 128, fr, fast_nodes=False)
+    scaled.set_scales(np.ones(8, np.float32))
+    assert lib.polar_plan_set_exact(scaled.handle, 1) == ps.POLAR_EINVAL
+    ex = ps.Plan(256, 128, fr, fast_nodes=False, exact=True)
+    assert ex.exact
+    with pytest.raises(ps.PolarError):
+        ex.set_scales(np.ones(8, np.float32))
+    with pytest.raises(ps.PolarError) as e:
+        ps.PlanSet([ex])
+    assert e.value.rc == ps.POLAR_EINVAL

@@ -82,3 +82,34 @@ def test_exact_noiseless_round_trip(oracle_lib):
     for b in range(5):
         st, out, pm = oracle_lib.scs_decode_exact(llr[b], N, K, fr, D=4, L=2, precision="f32")
         assert st == 0 and np.array_equal(out, cw[b])
+
+
+# ----------------------------------------------------------------- GPU part
+@pytest.mark.gpu
+@pytest.mark.parametrize("N,K,D,L,B", [(64, 32, 8, 4, 400), (256, 128, 16, 4, 200), (512, 256, 32, 8, 60),
+                                       (1024, 512, 32, 32, 40)])
+def test_gpu_exact_f_parity(oracle_lib, N, K, D, L, B):
+    """polar_plan_set_exact: same decisions as the float oracle (decoded
+    message, status) and path metrics within 1e-5 relative (the two sides'
+    log1p/exp differ in the last bits)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1809_03606_gb300 as ps
+
+    ps.load(build_if_missing=True)
+    fr = oracle_lib.construct(N, K, 0.0)
+    A = np.nonzero(fr == 0)[0]
+    plan = ps.Plan(N, K, fr, fast_nodes=False, exact=True)
+    for ebn0 in (1.0, 2.5):
+        llr = _llr(N, K, fr, B, ebn0, 11 * N + D, oracle_lib)
+        info, pm, st = ps.decode(plan, torch.from_numpy(llr).cuda(), D, L)
+        torch.cuda.synchronize()
+        got = ps.unpack_bits(info.cpu().numpy(), K)
+        pm = pm.cpu().numpy()
+        st = st.cpu().numpy()
+        for b in range(B):
+            rs, cw, rpm = oracle_lib.scs_decode_exact(llr[b], N, K, fr, D=D, L=L, precision="f32")
+            assert rs == 0 and st[b] == 0
+            assert np.array_equal(got[b], oracle_lib.encode(cw)[A]), b
+            assert abs(float(pm[b]) - float(rpm)) <= 1e-5 * max(1.0, abs(float(rpm))), (b, pm[b], rpm)
