@@ -628,6 +628,8 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
                                              uint32_t base, uint32_t slot, int D, int lane) {
     const int nfree = D - count;
     const int nb = c.nc < nfree ? c.nc : nfree;
+    // lane r forms candidate r's metric once; the loops below read it
+    const uint32_t my_pmb = __float_as_uint(__fadd_rn(pm, c.delta(lane < c.nc ? lane : 0)));
     if (nb > 0) {
         const uint32_t lt = (1u << lane) - 1u;
         int before = 0;  // free slots in the rows above
@@ -636,8 +638,9 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
             const bool f = st.pm[j] == EMPTY && slot_exists(j, lane, D);
             const uint32_t bj = __ballot_sync(FULL, f);
             const int r = before + __popc(bj & lt);
+            const uint32_t rpmb = __shfl_sync(FULL, my_pmb, r & 31);
             if (f && r < nb) {
-                st.pm[j] = __float_as_uint(__fadd_rn(pm, c.delta(r)));
+                st.pm[j] = rpmb;
                 st.meta[j] = meta;
                 st.seq[j] = base + uint32_t(c.nc - 1 - r);
                 st.aux[j] = slot | (c.mask(r) << 8);
@@ -652,7 +655,7 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
     int lj = 0;
     bool stale = true;
     for (int k = nb; k < c.nc; ++k) {
-        const uint32_t pmb = __float_as_uint(__fadd_rn(pm, c.delta(k)));
+        const uint32_t pmb = __shfl_sync(FULL, my_pmb, k);
         if (stale) {
             const bool e0 = slot_exists(0, lane, D);
             lw = e0 ? st.pm[0] : 0u;
