@@ -392,12 +392,13 @@ def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
 def bench_e2e(ps, plan, llrs, w, args, world: int):
     """Same metric through the C ABI with host buffers: every step copies its
     LLRs from pinned host memory and reads the results back, in chunks whose
-    copies overlap the decode of the previous chunk."""
+    copies overlap the decode of the previous chunk; consecutive chunks decode
+    on two streams, so the tail of one launch overlaps the next."""
     import torch
 
     B, N = w["frames"], w["N"]
     npts = len(llrs)
-    chunk = min(B, 1 << 17)
+    chunk = min(B, 1 << 18)
     host = []
     for l in llrs:
         h = torch.empty((B, N), dtype=torch.float32, pin_memory=True)
@@ -410,11 +411,12 @@ def bench_e2e(ps, plan, llrs, w, args, world: int):
     dout = [(torch.empty((chunk, plan.msg_words), dtype=torch.int32, device="cuda"),
              torch.empty(chunk, dtype=torch.float32, device="cuda"), torch.empty(chunk, dtype=torch.int8, device="cuda"))
             for _ in range(2)]
-    copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
+    copy_s = torch.cuda.Stream()
+    comp = [torch.cuda.Stream(), torch.cuda.Stream()]
     ready = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
-    for e in free:
-        e.record(comp_s)
+    for j, e in enumerate(free):
+        e.record(comp[j])
 
     def one_step():
         i = 0
@@ -426,13 +428,14 @@ def bench_e2e(ps, plan, llrs, w, args, world: int):
                     copy_s.wait_event(free[j])
                     dbuf[j][: hi - lo].copy_(host[p][lo:hi], non_blocking=True)
                     ready[j].record(copy_s)
-                with torch.cuda.stream(comp_s):
-                    comp_s.wait_event(ready[j])
+                cs = comp[j]
+                with torch.cuda.stream(cs):
+                    cs.wait_event(ready[j])
                     o = [t[: hi - lo] for t in dout[j]]
-                    ps.scs_decode_batch(plan, dbuf[j][: hi - lo], w["D"], w["L"], *o, stream=comp_s)
+                    ps.scs_decode_batch(plan, dbuf[j][: hi - lo], w["D"], w["L"], *o, stream=cs)
                     for src, dst in zip(o, out_host[p]):
                         dst[lo:hi].copy_(src, non_blocking=True)
-                    free[j].record(comp_s)
+                    free[j].record(cs)
                 i += 1
 
     steps = max(1, min(args.steps, 3))

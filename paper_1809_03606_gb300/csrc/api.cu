@@ -85,7 +85,7 @@ int plan_device(const polar_plan *p, const DeviceTables **out) {
     if (p->dev.device >= 0) return POLAR_EINVAL;  // a plan serves one device
     DeviceTables d{};
     d.device = dev;
-    e = upload(&d.ops, p->ops);
+    e = upload(&d.ops, p->dev_ops);
     if (e == cudaSuccess) e = upload(&d.crc_rows, p->crc_rows);
     if (e == cudaSuccess) e = upload(&d.msg_pos, p->msg_pos);
     if (e == cudaSuccess) e = upload(&d.info_pos, p->info_pos);

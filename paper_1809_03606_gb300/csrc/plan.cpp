@@ -163,6 +163,34 @@ extern "C" int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_n
             p->ops[size_t(t)].z = next;
         }
 
+        // the kernels' schedule: COMB runs and alpha descents merged into one
+        // entry (a path resumes only right after a branching operation, i.e.
+        // at the start of a run, so every resume point survives the merge)
+        for (int t = 0; t < nops;) {
+            KOp o = p->ops[size_t(t)];
+            const uint32_t code = o.x & 0xFFu;
+            const int lam = int((o.x >> 8) & 0xFFu);
+            const uint32_t s = o.y;
+            int k = 1;
+            auto at = [&](int q, uint32_t c, int l, uint32_t st) {
+                const KOp &n = p->ops[size_t(q)];
+                return (n.x & 0xFFFFu) == (c | uint32_t(l) << 8) && n.y == st;
+            };
+            if (code == OP_COMB) {
+                uint32_t st = s;
+                while (t + k < nops && k < 256 && lam + k < 32 && (st >= (1u << (lam + k - 1))) &&
+                       at(t + k, OP_COMB, lam + k, st - (1u << (lam + k - 1)))) {
+                    st -= 1u << (lam + k - 1);
+                    ++k;
+                }
+            } else if (code == OP_F || code == OP_G) {
+                while (t + k < nops && k < 256 && lam - k >= 0 && at(t + k, OP_F, lam - k, s)) ++k;
+            }
+            o.x |= uint32_t(k - 1) << 16;
+            p->dev_ops.push_back(o);
+            t += k;
+        }
+
         // information and message positions
         for (int i = 0; i < N; ++i)
             if (!p->frozen[size_t(i)]) p->info_pos.push_back(uint16_t(i));

@@ -34,6 +34,10 @@ constexpr uint32_t NO_TARGET = 0xFFFFFFFFu;
 //  z: alpha restore target for a path resuming at this op: the node whose
 //     alpha the next alpha-reading op needs, as lambda | s << 8, or NO_TARGET
 //  w: branching ordinal (index of the visit counter) for codes >= OP_BRANCH
+// The kernels read the schedule with runs merged (polar_plan::dev_ops): bits
+// 16..23 of x hold run - 1, where a COMB run climbs one stage per step (the
+// next odd child starts 2^lambda leaves earlier) and an alpha run is an F or
+// G followed by F ops one stage lower each (same first leaf).
 struct alignas(16) KOp {
     uint32_t x, y, z, w;
 };
@@ -57,7 +61,8 @@ struct polar_plan {
     int W = 0;        // 32-bit words of a packed N-bit array (at least 1)
     int nbranch = 0;  // branching operations (visit counters)
     std::vector<uint8_t> frozen;
-    std::vector<polarscs::KOp> ops;
+    std::vector<polarscs::KOp> ops;      // the schedule, one entry per operation
+    std::vector<polarscs::KOp> dev_ops;  // the kernels' schedule: runs merged
     std::vector<uint32_t> crc_rows;
     std::vector<uint16_t> msg_pos, info_pos;
     std::vector<uint32_t> crc_contrib;

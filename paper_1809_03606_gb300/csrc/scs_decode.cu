@@ -919,7 +919,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         uint4 op = nxt;
         for (;;) {
             uint32_t code;
-            int lam, s;
+            int lam, s, run = 1;
             const bool sched = rl < lam_d;  // else: a recomputed spine stage
             if (!sched) {
                 lam = rl;
@@ -933,20 +933,25 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
                 code = op.x & 0xFFu;
                 lam = int((op.x >> 8) & 0xFFu);
                 s = int(op.y);
+                run = int((op.x >> 16) & 0xFFu) + 1;
                 if (code >= OP_BRANCH) break;
                 ++t;
             }
-            if (code == OP_F) {
-                w.template op_f<EXACT>(lam);
-                if (sched) ops += 2u << lam;
+            if (code <= OP_G) {  // an F or G, then run - 1 F ops down the left edge
+                #pragma unroll 1
+                for (int i = 0; i < run; ++i) {
+                    if (i == 0 && code == OP_G) w.op_g(lam, s);
+                    else w.template op_f<EXACT>(lam - i);
+                    if (sched) ops += 2u << (lam - i);
+                }
                 PT(PH_FG)
-            } else if (code == OP_G) {
-                w.op_g(lam, s);
-                if (sched) ops += 2u << lam;
-                PT(PH_FG)
-            } else if (code == OP_COMB) {
-                w.op_comb(lam, s);
-                ops += (lam < 5) ? 1u : (1u << (lam - 5));
+            } else if (code == OP_COMB) {  // run combines, one stage up each
+                #pragma unroll 1
+                for (int i = 0; i < run; ++i) {
+                    w.op_comb(lam + i, s);
+                    ops += (lam + i < 5) ? 1u : (1u << (lam + i - 5));
+                    s -= 1 << (lam + i);
+                }
                 PT(PH_COMB)
             } else {  // Rate-0 node or frozen leaf: beta = 0, PM += sum HD(a)|a|
                 const float pen = w.node_sum(lam, EXACT ? 3 : 1);
@@ -1230,7 +1235,7 @@ Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, co
     c.W = p->W;
     c.Kmsg = p->Kmsg;
     c.crc = p->crc;
-    c.nops = int(p->ops.size());
+    c.nops = int(p->dev_ops.size());
     c.nbranch = p->nbranch;
     c.info_words = (p->Kmsg + 31) / 32;
     c.snap_words = ((p->W + 4) + 7) & ~7;
@@ -1588,7 +1593,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     if (rc) return rc;
 
     // the plan's tables, copied into the static table area
-    const size_t ops_bytes = p->ops.size() * sizeof(KOp);
+    const size_t ops_bytes = p->dev_ops.size() * sizeof(KOp);
     const size_t rows_off = align_up(ops_bytes, 256);
     const size_t rows_bytes = p->crc_rows.size() * sizeof(uint32_t);
     const size_t pos_off = align_up(rows_off + rows_bytes, 256);
@@ -1631,7 +1636,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     a.scratch = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(areas.scratch) + 64);
     // tables from host memory, then the frame counter back to zero (the array
     // keeps whatever the previous call left in it)
-    e = cudaMemcpyAsync(tab, p->ops.data(), ops_bytes, cudaMemcpyHostToDevice, stream);
+    e = cudaMemcpyAsync(tab, p->dev_ops.data(), ops_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && rows_bytes)
         e = cudaMemcpyAsync(tab + rows_off, p->crc_rows.data(), rows_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && pos_bytes)
