@@ -511,6 +511,17 @@ struct Warp {
 
     // flip the candidate's positions relative to the node's hard decisions
     __device__ void apply_flips(uint32_t mask, const int *m, int s, int lam) const {
+        if (lam <= 5) {  // the node lies in one word: one masked XOR
+            if (lane == 0 && mask) {
+                uint32_t x = (mask & FLIP_ALL) ? ((lam == 5) ? FULL : ((1u << (1 << lam)) - 1u)) : 0u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if ((mask >> j) & 1u) x ^= 1u << m[j];
+                beta[s >> 5] ^= x << (s & 31);
+            }
+            __syncwarp();
+            return;
+        }
         if (mask & FLIP_ALL) {
             const int len = 1 << lam;
             if (len >= 32) {
@@ -725,7 +736,7 @@ __device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int
     __syncwarp();
 }
 
-template <int NS, bool EXACT>
+template <int NS, bool EXACT, bool STATS>
 __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Warp &w,
                                              unsigned b, uint32_t *orow) {
     const int lane = w.lane;
@@ -1080,7 +1091,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         if (status == POLAR_TIMEOUT) out_pm = __int_as_float(0x7f800000);
         a.pm_out[b] = out_pm;
         a.status_out[b] = int8_t(status);
-        if (a.stats_out) {
+        if (STATS && a.stats_out) {  // without counters all counting is dead code
             uint32_t *sr = a.stats_out + size_t(b) * 4;
             sr[0] = n_iter;
             sr[1] = n_switch;
@@ -1097,7 +1108,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
 // MIXED = false: every frame uses a.code, a.D, a.L and row b of the LLR and
 // message buffers.  MIXED = true: frame b has its own code, D and L
 // (a.frames[b]) and offsets into packed LLR and message buffers.
-template <bool MIXED, int NS, bool EXACT = false>
+template <bool MIXED, int NS, bool EXACT, bool STATS>
 __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Code codes_s[MIXED ? kMaxCodes : 1];
@@ -1123,7 +1134,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const Code &c = a.code;
                 Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                        my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
-                decode_frame<NS, EXACT>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
+                decode_frame<NS, EXACT, STATS>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
             } else {
                 const int4 fd = a.frames[b];
                 if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
@@ -1137,7 +1148,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const long long lo = a.llr_off[b];
                 Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
                        reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales};
-                decode_frame<NS, false>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
+                decode_frame<NS, false, STATS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
             }
         }
     }
@@ -1208,7 +1219,7 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
             __syncwarp();
             Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                    my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
-            decode_frame<NS, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
+            decode_frame<NS, false, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
         }
         if (lane == 0) {
             a.t_done[k] = global_ns();
@@ -1245,23 +1256,45 @@ Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, co
 
 int warp_smem_bytes(int N, int W, int nbranch) { return ((4 * N + 4 * W + nbranch) + 15) & ~15; }
 
-// block size and persistent grid for a kernel with `warp_smem` bytes per warp
-template <bool MIXED, int NS, bool EXACT = false>
-int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int *smem_out) {
+// The instantiation of the decoder for one launch: mixed or uniform, one or
+// two stack rows per lane, exact-f or min-sum, with or without counters.
+template <bool MIXED, int NS, bool EXACT, bool STATS>
+const void *kernel_fn() {
+    return reinterpret_cast<const void *>(scs_decode_kernel<MIXED, NS, EXACT, STATS>);
+}
+
+const void *uniform_kernel(const polar_plan *p, int D, bool stats) {
+    const bool two = D > 32;
+    if (p->exact) {
+        if (two) return stats ? kernel_fn<false, 2, true, true>() : kernel_fn<false, 2, true, false>();
+        return stats ? kernel_fn<false, 1, true, true>() : kernel_fn<false, 1, true, false>();
+    }
+    if (two) return stats ? kernel_fn<false, 2, false, true>() : kernel_fn<false, 2, false, false>();
+    return stats ? kernel_fn<false, 1, false, true>() : kernel_fn<false, 1, false, false>();
+}
+
+const void *mixed_kernel(int Dmax, bool stats) {
+    if (Dmax > 32) return stats ? kernel_fn<true, 2, false, true>() : kernel_fn<true, 2, false, false>();
+    return stats ? kernel_fn<true, 1, false, true>() : kernel_fn<true, 1, false, false>();
+}
+
+// block size and persistent grid for kernel `fn` with `warp_smem` bytes per warp
+int launch_shape(const void *fn, bool mixed, int warp_smem, int B, int wpb, int *grid_out, int *wpb_out,
+                 int *smem_out) {
     int dev = 0, sms = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int static_smem = MIXED ? int(sizeof(Code)) * kMaxCodes : int(sizeof(Code));
+    const int static_smem = mixed ? int(sizeof(Code)) * kMaxCodes : int(sizeof(Code));
     while (wpb > 1 && wpb * warp_smem + static_smem > max_smem) wpb >>= 1;
     if (wpb * warp_smem + static_smem > max_smem) return POLAR_ELIMIT;
     const int smem = wpb * warp_smem;
-    e = cudaFuncSetAttribute(scs_decode_kernel<MIXED, NS, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scs_decode_kernel<MIXED, NS, EXACT>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return POLAR_ELIMIT;
     long long grid = (long long)sms * per_sm;
@@ -1273,24 +1306,10 @@ int launch_shape(int warp_smem, int B, int wpb, int *grid_out, int *wpb_out, int
     return 0;
 }
 
-// the uniform kernel for a plan: stack rows by D, exact-f or min-sum by plan
-int uniform_shape(const polar_plan *p, int warp_smem, int B, int D, int wpb, int *grid, int *wpb_out, int *smem) {
-    if (p->exact)
-        return D <= 32 ? launch_shape<false, 1, true>(warp_smem, B, wpb, grid, wpb_out, smem)
-                       : launch_shape<false, 2, true>(warp_smem, B, wpb, grid, wpb_out, smem);
-    return D <= 32 ? launch_shape<false, 1>(warp_smem, B, wpb, grid, wpb_out, smem)
-                   : launch_shape<false, 2>(warp_smem, B, wpb, grid, wpb_out, smem);
-}
-
-void launch_uniform(const polar_plan *p, int D, int grid, int wpb, int smem, cudaStream_t stream, const Args &a) {
-    const dim3 g(static_cast<unsigned>(grid)), b(static_cast<unsigned>(wpb * 32));
-    if (p->exact) {
-        if (D <= 32) scs_decode_kernel<false, 1, true><<<g, b, size_t(smem), stream>>>(a);
-        else scs_decode_kernel<false, 2, true><<<g, b, size_t(smem), stream>>>(a);
-    } else {
-        if (D <= 32) scs_decode_kernel<false, 1><<<g, b, size_t(smem), stream>>>(a);
-        else scs_decode_kernel<false, 2><<<g, b, size_t(smem), stream>>>(a);
-    }
+cudaError_t launch_fn(const void *fn, int grid, int wpb, int smem, cudaStream_t stream, Args &a) {
+    void *args[] = {&a};
+    return cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(static_cast<unsigned>(wpb * 32)), args,
+                            size_t(smem), stream);
 }
 
 int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *d_llr, int B, int D, int L,
@@ -1312,7 +1331,8 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
 
     int grid = 0, wpb = 0, smem = 0;
-    int rc = uniform_shape(p, a.warp_smem, B, D, 4, &grid, &wpb, &smem);
+    const void *fn = uniform_kernel(p, D, d_stats != nullptr);
+    int rc = launch_shape(fn, false, a.warp_smem, B, 4, &grid, &wpb, &smem);
     if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1326,8 +1346,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
     e = cudaMemsetAsync(ws, 0, 64, stream);
     if (e == cudaSuccess) {
-        launch_uniform(p, D, grid, wpb, smem, stream, a);
-        e = cudaGetLastError();
+        e = launch_fn(fn, grid, wpb, smem, stream, a);
     }
     cudaError_t e2 = cudaFreeAsync(ws, stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -1420,8 +1439,8 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
 
     int grid = 0, wpb = 0, smem = 0;
     const int nb_units = (B + chunk - 1) / chunk;
-    int rc = Dmax <= 32 ? launch_shape<true, 1>(a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem)
-                        : launch_shape<true, 2>(a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem);
+    const void *fn = mixed_kernel(Dmax, d_stats != nullptr);
+    int rc = launch_shape(fn, true, a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem);
     if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1435,9 +1454,7 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     a.scratch = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + 64);
     e = cudaMemsetAsync(ws, 0, 64, stream);
     if (e == cudaSuccess) {
-        if (Dmax <= 32) scs_decode_kernel<true, 1><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
-        else scs_decode_kernel<true, 2><<<unsigned(grid), unsigned(wpb * 32), size_t(smem), stream>>>(a);
-        e = cudaGetLastError();
+        e = launch_fn(fn, grid, wpb, smem, stream, a);
     }
     cudaError_t e2 = cudaFreeAsync(ws, stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -1627,7 +1644,8 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     int wpb = 4;
     while (wpb > 1 && size_t(wpb) > warps_fit) wpb >>= 1;
     int grid = 0, smem = 0;
-    rc = uniform_shape(p, a.warp_smem, B, D, wpb, &grid, &wpb, &smem);
+    const void *fn = uniform_kernel(p, D, d_stats != nullptr);
+    rc = launch_shape(fn, false, a.warp_smem, B, wpb, &grid, &wpb, &smem);
     if (rc) return rc;
     const long long fit = (long long)(warps_fit / size_t(wpb));
     if (fit < grid) grid = int(fit);
@@ -1645,8 +1663,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
         e = cudaMemcpyAsync(tab + sc_off, p->scales.data(), sc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    launch_uniform(p, D, grid, wpb, smem, stream, a);
-    e = cudaGetLastError();
+    e = launch_fn(fn, grid, wpb, smem, stream, a);
     return e == cudaSuccess ? 0 : cuda_status(e);
 }
 
