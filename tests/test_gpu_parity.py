@@ -201,3 +201,23 @@ def test_scaled_min_sum_parity(oracle_lib, N, K, crc, fast, D, L):
     m_u, pm_u, st_u, _ = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=fast, D=D, L=L, crc_len=crc, threads=8)
     assert np.array_equal(ps.unpack_bits(info2.cpu().numpy(), K - crc), m_u)
     assert np.array_equal(pm2.cpu().numpy().view(np.uint32), pm_u.view(np.uint32))
+
+
+def test_full_size_launch(oracle_lib):
+    """The bench's launch: 1,048,576 frames of PC(1024,512) CRC-16, D = L = 32,
+    at 1.5 dB (the hardest point) in one scs_decode_batch call.  The batch
+    tiles 4,096 host-made frames 256 times, so every one of the 2^20 outputs
+    has an oracle value (that of its row modulo 4,096)."""
+    N, K, crc, D, L = 1024, 512, 16, 32, 32
+    base = 4096
+    fr, msg, cw, llr = make_frames(oracle_lib, N, K, crc, base, 1.5, seed=77)
+    m_o, pm_o, st_o, _ = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=True, D=D, L=L, crc_len=crc, threads=8)
+    plan = ps.Plan(N, K, fr, fast_nodes=True, crc=crc)
+    x = torch.from_numpy(llr).cuda().repeat(256, 1)
+    info, pm, st = ps.decode(plan, x, D, L)
+    torch.cuda.synchronize()
+    del x
+    words_o = torch.from_numpy(ps.pack_bits(m_o)).cuda().repeat(256, 1)
+    assert torch.equal(info, words_o)
+    assert torch.equal(pm.view(torch.int32), torch.from_numpy(pm_o.view(np.int32)).cuda().repeat(256))
+    assert torch.equal(st, torch.from_numpy(st_o).cuda().repeat(256))
