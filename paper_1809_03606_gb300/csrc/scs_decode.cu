@@ -660,12 +660,31 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
         }
         count += nb;
     }
-    // the worst entry's metric is found again only after a replacement (a
-    // rejected candidate leaves the stack as it was)
+    // a full stack: only candidates below the current worst entry can enter,
+    // and the worst only falls as they do, so the others are skipped at once;
+    // the worst entry is found again only after a replacement
     uint32_t lw = 0u, ls = EMPTY, gw = 0u;
     int lj = 0;
     bool stale = true;
-    for (int k = nb; k < c.nc; ++k) {
+    uint32_t todo = 0u;  // candidates below the worst entry (it only decreases)
+    if (nb < c.nc) {
+        const bool e0 = slot_exists(0, lane, D);
+        lw = e0 ? st.pm[0] : 0u;
+        ls = e0 ? st.seq[0] : EMPTY;
+#pragma unroll
+        for (int j = 1; j < NS; ++j)
+            if (slot_exists(j, lane, D) && (st.pm[j] > lw || (st.pm[j] == lw && st.seq[j] < ls))) {
+                lw = st.pm[j];
+                ls = st.seq[j];
+                lj = j;
+            }
+        gw = __reduce_max_sync(FULL, lw);
+        stale = false;
+        todo = __ballot_sync(FULL, lane >= nb && lane < c.nc && my_pmb < gw);
+    }
+    while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1u;
         const uint32_t pmb = __shfl_sync(FULL, my_pmb, k);
         if (stale) {
             const bool e0 = slot_exists(0, lane, D);
