@@ -715,7 +715,7 @@ static int scs_run(or_dec *d, const float *llr, uint8_t *msg_out, float *pm_out,
             }
             continue;
         }
-        /* walk the schedule up to the next branching node */
+        /* walk the schedule up to the next branching node (Sec. 4) */
         int switched = 1; /* the oracle always recomputes alpha from the root */
         int t = sched;
         for (; t < d->nops; t++) {

@@ -941,7 +941,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         }
         PT(PH_ALPHA)
 
-        // ---- walk the schedule to the next branching node ----
+        // ---- walk the schedule to the next branching node (Sec. 4) ----
         float pm = __uint_as_float(p_pmb);
         int t = p_sched;
         const uint4 *opsv = reinterpret_cast<const uint4 *>(c.ops);
