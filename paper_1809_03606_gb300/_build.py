@@ -22,7 +22,8 @@ LIB = os.path.join(BUILD, "libpolarscs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["plan.cpp", "api.cu", "scs_decode.cu", "encode.cu", "gsc.cu", "serve.cpp"]
 # -fmad=false: the decoder's float arithmetic must not be contracted (bit
-# parity with the CPU oracle); nothing in these kernels multiplies and adds.
+# parity with the CPU oracle): its only products, the optional stage scales,
+# are rounded on their own before any sum.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
 
