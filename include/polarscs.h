@@ -15,7 +15,10 @@
  *    information positions.  Message bit j sits on the j-th information index
  *    in increasing order.
  *  - Codewords are c = u F^{(x)n} with the XOR tree of Fig. encoder
- *    (non-systematic encoding).
+ *    (non-systematic encoding), or systematic ones for a plan switched by
+ *    polar_plan_set_systematic.
+ *  - Decoding uses min-sum (Eq. minsum) unless a plan is switched to the
+ *    exact box-plus rule by polar_plan_set_exact.
  *  - Channel LLRs are float32, LLR = ln P(0)/P(1); they must be finite.
  *  - Device buffers are row-major per frame.  Packed bit buffers are uint32
  *    words, bit j of a row in word j/32 at bit position j%32 (LSB first).
