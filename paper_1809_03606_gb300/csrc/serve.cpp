@@ -4,8 +4,10 @@
 //
 // polar_serve: requests arrive at given times.  A producer loop releases each
 // request once it has arrived and the LLR arena (a fixed HBM budget) has room
-// for it: its LLRs are copied into the arena and a published-count is
-// advanced on the device.  One persistent kernel (scs_serve_kernel) keeps
+// for it: the batch of requests released together is gathered into a pinned
+// host mirror of the arena (same offsets), copied to the arena in one
+// transfer (two when it wraps), and a published-count is advanced on the
+// device behind it on the same stream.  One persistent kernel (scs_serve_kernel) keeps
 // every warp busy: a warp that finishes a request claims the next index,
 // waits (bounded) until it is published, and decodes it, so new requests
 // start while older ones are still on the GPU.  Arena space is handed out in
@@ -67,12 +69,6 @@ struct HostBuf {
         if (p) cudaFreeHost(p);
     }
     cudaError_t alloc(size_t bytes, unsigned flags) { return cudaHostAlloc(&p, bytes < 16 ? 16 : bytes, flags); }
-};
-struct Registered {
-    const void *p = nullptr;
-    ~Registered() {
-        if (p) cudaHostUnregister(const_cast<void *>(p));
-    }
 };
 
 // request layout shared by both engines: sizes, arena placement (contiguous,
@@ -153,20 +149,9 @@ extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const 
     if (info_off)
         for (int r = 0; r < R; ++r) out_words = std::max(out_words, ioff[size_t(r)] + lay.words[size_t(r)]);
 
-    // pool extent (registered for asynchronous copies)
-    long long pool_end = 0;
-    for (int r = 0; r < R; ++r) {
-        const int p = req[4 * size_t(r) + 3];
-        pool_end = std::max(pool_end, (long long)pool_off[p] + lay.N[size_t(r)]);
-    }
-    Registered reg;
-    cudaError_t e = cudaHostRegister(const_cast<float *>(pool_llr), size_t(pool_end) * 4, cudaHostRegisterDefault);
-    if (e == cudaSuccess) reg.p = pool_llr;
-    else if (e == cudaErrorHostMemoryAlreadyRegistered) cudaGetLastError();
-    else return cuda_status(e);
-
+    cudaError_t e = cudaSuccess;
     DevBuf d_arena, d_frames, d_loff, d_ioff, d_info, d_pm, d_st, d_tdone, d_head, d_err, d_cnt, d_scr, d_gt;
-    HostBuf h_done, h_abort, h_head, h_tdone;
+    HostBuf h_done, h_abort, h_head, h_tdone, h_mirror;
     const size_t scr_bytes = serve_scratch_bytes(set, Dmax);
     if ((e = d_arena.alloc(size_t(arena_floats) * 4)) != cudaSuccess || (e = d_frames.alloc(sizeof(int4) * R)) ||
         (e = d_loff.alloc(8 * size_t(R))) || (e = d_ioff.alloc(8 * size_t(R))) ||
@@ -174,8 +159,9 @@ extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const 
         (e = d_tdone.alloc(8 * size_t(R))) || (e = d_head.alloc(8)) || (e = d_err.alloc(4)) || (e = d_cnt.alloc(4)) ||
         (e = d_scr.alloc(scr_bytes)) || (e = d_gt.alloc(8)) || (e = h_done.alloc(size_t(R), cudaHostAllocMapped)) ||
         (e = h_abort.alloc(4, cudaHostAllocMapped)) || (e = h_head.alloc(8 * 4096, 0)) ||
-        (e = h_tdone.alloc(8 * size_t(R), 0)))
+        (e = h_tdone.alloc(8 * size_t(R), 0)) || (e = h_mirror.alloc(size_t(arena_floats) * 4, 0)))
         return cuda_status(e);
+    float *mirror = static_cast<float *>(h_mirror.p);
     volatile unsigned char *done = static_cast<volatile unsigned char *>(h_done.p);
     volatile int *abort_flag = static_cast<volatile int *>(h_abort.p);
     std::memset(h_done.p, 0, size_t(R));
@@ -263,19 +249,23 @@ extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const 
             std::this_thread::sleep_for(std::chrono::microseconds(2));
             continue;
         }
-        // copy the new requests' LLRs in maximal runs contiguous in pool and arena
+        // gather the new requests' LLRs into the mirror (their arena
+        // places are free: arena admission returned them only after the
+        // requests that used them completed, copies included), then copy
+        // each run contiguous in the arena (one, two when the batch wraps)
+        for (int q = published; q < r_end; ++q)
+            std::memcpy(mirror + lay.off[size_t(q)], pool_llr + pool_off[req[4 * size_t(q) + 3]],
+                        size_t(lay.N[size_t(q)]) * 4);
         int r = published;
         while (r < r_end && e == cudaSuccess) {
             int q = r + 1;
-            const long long src0 = pool_off[req[4 * size_t(r) + 3]];
             long long len = lay.N[size_t(r)];
-            while (q < r_end && pool_off[req[4 * size_t(q) + 3]] == src0 + len &&
-                   lay.off[size_t(q)] == lay.off[size_t(r)] + len) {
+            while (q < r_end && lay.off[size_t(q)] == lay.off[size_t(r)] + len) {
                 len += lay.N[size_t(q)];
                 ++q;
             }
-            e = cudaMemcpyAsync(static_cast<float *>(d_arena.p) + lay.off[size_t(r)], pool_llr + src0, size_t(len) * 4,
-                                cudaMemcpyHostToDevice, cs);
+            e = cudaMemcpyAsync(static_cast<float *>(d_arena.p) + lay.off[size_t(r)], mirror + lay.off[size_t(r)],
+                                size_t(len) * 4, cudaMemcpyHostToDevice, cs);
             r = q;
         }
         head_stage[slot] = (unsigned long long)r_end;
