@@ -87,7 +87,7 @@ def test_exact_noiseless_round_trip(oracle_lib):
 # ----------------------------------------------------------------- GPU part
 @pytest.mark.gpu
 @pytest.mark.parametrize("N,K,D,L,B", [(64, 32, 8, 4, 400), (256, 128, 16, 4, 200), (512, 256, 32, 8, 60),
-                                       (1024, 512, 32, 32, 40)])
+                                       (1024, 512, 32, 32, 40), (256, 128, 48, 8, 100)])
 def test_gpu_exact_f_parity(oracle_lib, N, K, D, L, B):
     """polar_plan_set_exact: same decisions as the float oracle (decoded
     message, status) and path metrics within 1e-5 relative (the two sides'

@@ -160,3 +160,41 @@ def test_mixed_graph_replay_and_tuner(lib, oracle_lib):
         torch.cuda.synchronize()
         for r, x in zip(ref, (mb.info, mb.pm, mb.status)):
             assert torch.equal(r, x)
+
+
+@pytest.mark.gpu
+def test_mixed_with_systematic_plans(lib, oracle_lib):
+    """Systematic and non-systematic plans in one launch: every frame equals
+    the oracle's decode with its own encoding, D and L."""
+    torch = pytest.importorskip("torch")
+    codes = [(256, 128, 8, True), (512, 256, 8, False), (1024, 512, 16, True), (128, 64, 0, True)]
+    rng = np.random.default_rng(12)
+    B = 800
+    plans, frozens = [], []
+    for N, K, crc, sysf in codes:
+        fr = oracle_lib.construct(N, K, 0.0)
+        frozens.append(fr)
+        plans.append(ps.Plan(N, K, fr, fast_nodes=True, crc=crc, systematic=sysf))
+    idx = rng.integers(0, len(codes), B).astype(np.int32)
+    D = rng.integers(1, 65, B).astype(np.int32)
+    L = rng.integers(1, 65, B).astype(np.int32)
+    rows, msgs = [None] * B, [None] * B
+    for ci, (N, K, crc, sysf) in enumerate(codes):
+        sel = np.nonzero(idx == ci)[0]
+        msg = W.message_bits(90 + ci, sel.size, K - crc)
+        cw = oracle_lib.encode_batch(msg, N, K, frozens[ci], crc, systematic=sysf)
+        llr = W.bpsk_awgn_llr(cw, W.awgn_noise(90 + ci, sel.size, N), W.sigma_from_ebn0(2.0, K / N))
+        for j, b in enumerate(sel):
+            rows[b], msgs[b] = llr[j], msg[j]
+    pset = ps.PlanSet(plans)
+    mb = ps.MixedBatch(pset, idx, D, L, rows)
+    mb.decode(pset)
+    torch.cuda.synchronize()
+    pm, st = mb.pm.cpu().numpy(), mb.status.cpu().numpy()
+    for b in range(B):
+        N, K, crc, sysf = codes[idx[b]]
+        st_o, m_o, pm_o, _, _ = oracle_lib.scs_decode(rows[b], N, K, frozens[idx[b]], fast=True, D=int(D[b]),
+                                                      L=int(L[b]), crc_len=crc, systematic=sysf)
+        got = ps.unpack_bits(mb.message_words(b)[None, :], K - crc)[0]
+        assert np.array_equal(got, m_o), b
+        assert pm[b].view(np.uint32) == pm_o.view(np.uint32) and st[b] == st_o, b
