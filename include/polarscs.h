@@ -268,15 +268,18 @@ int gsc_loss_grad_f64(const polar_plan *plan, const double *d_llr, const uint32_
  * Not a construct of the paper: a serving form of the same decoder.  Requests
  * arrive at given times (seconds from the start of the call, non-decreasing).
  * Request r is (plan index in the set, D, L, pool frame) = req[4r .. 4r+3];
- * its N LLRs are pool_llr[pool_off[frame] ..] (host memory; registered for
- * asynchronous copies during the call).
+ * its N LLRs are pool_llr[pool_off[frame] ..] (host memory, read during the
+ * call).
  *  polar_serve keeps one persistent kernel resident: each warp claims the
  *  next request, waits until the host has released it, decodes it and
  *  raises its completion flag, so requests that arrive while others are
  *  being decoded start as soon as a warp and arena space free up.  A request
  *  is released once it has arrived and its LLRs fit in the device arena of
  *  arena_floats floats (the HBM budget; space is returned when the oldest
- *  outstanding requests complete).  Every device and host wait is bounded by
+ *  outstanding requests complete).  The requests released together are
+ *  gathered on the host into a pinned mirror of the arena (arena_floats
+ *  floats of pinned host memory for the duration of the call) and copied in
+ *  one transfer.  Every device and host wait is bounded by
  *  wait_s seconds; on time-out the engine stops and returns POLAR_ETIMEOUT.
  *  polar_serve_baseline decodes one size per launch: every interval_s the
  *  arrived requests are grouped by (plan, D, L) and each group is a separate
