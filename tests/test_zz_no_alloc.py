@@ -75,3 +75,28 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     assert lib.scs_decode_batch_noalloc(plan.handle, dummy, 4, 0, 4, dummy, dummy, dummy, None, None) == ps.POLAR_EINVAL
     big = ps.Plan(16384, 8192, ps.polar_construct(16384, 8192, 0.0))
     assert lib.scs_decode_batch_noalloc(big.handle, dummy, 1, 8, 8, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
+
+
+def test_noalloc_plan_modes(oracle_lib):
+    """Systematic and exact-f plans through the allocation-free entry point
+    give exactly the regular entry point's outputs."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ps.load(build_if_missing=True)
+    modes = [dict(N=512, K=256, crc=8, fast=True, systematic=True, exact=False, D=32, L=16, B=1500),
+             dict(N=256, K=128, crc=0, fast=False, systematic=False, exact=True, D=16, L=4, B=800)]
+    for m in modes:
+        fr = oracle_lib.construct(m["N"], m["K"], 0.0)
+        msg = W.message_bits(7, m["B"], m["K"] - m["crc"])
+        cw = oracle_lib.encode_batch(msg, m["N"], m["K"], fr, m["crc"], systematic=m["systematic"])
+        llr = W.bpsk_awgn_llr(cw, W.awgn_noise(7, m["B"], m["N"]), W.sigma_from_ebn0(2.0, m["K"] / m["N"]))
+        plan = ps.Plan(m["N"], m["K"], fr, fast_nodes=m["fast"], crc=m["crc"], systematic=m["systematic"],
+                       exact=m["exact"])
+        x = torch.from_numpy(llr).cuda()
+        got, ref = _outputs(plan, m["B"]), _outputs(plan, m["B"])
+        ps.scs_decode_batch_noalloc(plan, x, m["D"], m["L"], *got)
+        ps.scs_decode_batch(plan, x, m["D"], m["L"], *ref)
+        torch.cuda.synchronize()
+        for r, q in zip(ref, got):
+            assert torch.equal(r, q), m
+        assert int((ref[2] == 0).sum()) > 0
