@@ -16,7 +16,9 @@
 // pass overwrites the stage values with their adjoints in place (a thread
 // reads and then writes the same two parent positions).  Per-frame sums go to
 // a [B, n+1] buffer that a second kernel reduces over frames in a fixed order,
-// so results do not depend on scheduling.  Templated on the value type:
+// so results do not depend on scheduling; inside a frame each warp reduces its
+// share by a shuffle tree and the warps' sums are added in warp order once per
+// frame (no block barrier per stage for the sums).  Templated on the value type:
 // float for training, double for gradient checks.
 #include <cuda_runtime.h>
 
@@ -53,22 +55,11 @@ __device__ __forceinline__ T softplus(T z) {
     return z > T(0) ? z + log1p(exp(-z)) : log1p(exp(z));
 }
 
-// block-wide sum in a fixed order (warp shuffle tree, then warps in order)
+// warp sum by a shuffle tree (the full sum ends in lane 0)
 template <typename T>
-__device__ T block_sum(T v, T *red) {
+__device__ __forceinline__ T warp_sum(T v) {
     for (int k = 16; k >= 1; k >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, k);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    T s = T(0);
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < int(blockDim.x >> 5); ++i) s += red[i];
-        red[32] = s;
-    }
-    __syncthreads();
-    s = red[32];
-    return s;
+    return v;
 }
 
 template <typename T>
@@ -76,8 +67,12 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
     extern __shared__ __align__(16) unsigned char gsm[];
     T *tree = reinterpret_cast<T *>(gsm);                           // (n+1) * N
     uint32_t *xs = reinterpret_cast<uint32_t *>(tree + (a.n + 1) * a.N);  // (n+1) * W partial sums
-    __shared__ T red[33];
+    // per-warp partial sums of the frame's loss and of d/ds_lambda, reduced
+    // over the warps once per frame (same fixed order as a block-wide sum)
+    constexpr int kWarps = kGscThreads / 32;
+    __shared__ T wsum[16 * kWarps];
     const int N = a.N, n = a.n, W = a.W, half = N >> 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
         const T *l = a.llr + size_t(b) * N;
         for (int i = threadIdx.x; i < N; i += blockDim.x) tree[size_t(n) * N + i] = l[i];
@@ -134,8 +129,8 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
             }
             if (a.with_grad) tree[i] = adj;
         }
-        const T fl = block_sum(loss, red);
-        if (threadIdx.x == 0) a.frame_sums[size_t(b) * (n + 1)] = fl;
+        loss = warp_sum(loss);
+        if (lane == 0) wsum[wid] = loss;
         if (a.with_grad) {
             __syncthreads();
             for (int lam = 0; lam < n; ++lam) {
@@ -159,12 +154,19 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
                     par[ps + j] = ax;
                     par[ps + len + j] = ay;
                 }
-                const T fg = block_sum(gs, red);
-                if (threadIdx.x == 0) a.frame_sums[size_t(b) * (n + 1) + 1 + lam] = fg;
+                gs = warp_sum(gs);
+                if (lane == 0) wsum[(1 + lam) * kWarps + wid] = gs;
                 __syncthreads();
             }
             if (a.grad_llr)
                 for (int i = threadIdx.x; i < N; i += blockDim.x) a.grad_llr[size_t(b) * N + i] = tree[size_t(n) * N + i];
+        }
+        __syncthreads();
+        const int nq = a.with_grad ? n + 1 : 1;
+        if (int(threadIdx.x) < nq) {
+            T sum = T(0);
+            for (int i = 0; i < kWarps; ++i) sum += wsum[threadIdx.x * kWarps + i];
+            a.frame_sums[size_t(b) * (n + 1) + threadIdx.x] = sum;
         }
         __syncthreads();
     }
