@@ -598,6 +598,26 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
         pm_per[bs_t] = p_
         st_per[bs_t] = s_
     same = bool(torch.equal(pm_per.view(torch.int32), pm.view(torch.int32)) and torch.equal(st_per, st))
+    # roofline of the mixed launch: counted operations (one untimed launch
+    # with counters) and algorithmic bytes against the same peaks as the sweep
+    stats = torch.empty((B, 4), dtype=torch.int32, device="cuda")
+    ps.scs_decode_mixed(*margs, stats=stats, order=order)
+    torch.cuda.synchronize()
+    ops_step = float((stats[:, 2].to(torch.int64) & 0xFFFFFFFF).sum().item())
+    del stats
+    bytes_step = float(sum(4 * int(n) for n in m["Ns"]) + 4 * int(m["words"].sum()) + 5 * B)
+    peaks = measured_peaks()
+    sms = ps.polar_device_info()["sm_count"]
+    alu_peak = sms * ALU_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6
+    t_alu, t_hbm = ops_step / alu_peak, bytes_step / (peaks["hbm_gbs"] * 1e9)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": ops_step / (ms_mixed / 1e3) / 1e12, "peak": alu_peak / 1e12, "unit": "Top/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_step / (ms_mixed / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    cpu = mixed_cpu_baseline(args.cpu_frames * 4) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     kmsg = torch.from_numpy((m["Ks"] - MIXED["crc"]).astype(np.int64)).sum().item()
     err = 0
     info_np = info.cpu().numpy()
@@ -617,7 +637,7 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
                            "speedup_vs_per_config": ms_per / ms_mixed, "identical_outputs": same,
                            "tuned": {"warps_per_block": wpb, "frames_per_claim": chunk},
                            "fer_sampled": fer, "crc_fail_rate": float((st != 0).double().mean().item())},
-                "clocks": sampler.summary() if sampler else None}
+                "roofline": roof, "cpu_baseline": cpu, "clocks": sampler.summary() if sampler else None}
         print(json.dumps(line), flush=True)
 
 
@@ -673,6 +693,24 @@ def bench_gsc(args, rank: int, world: int, local_rank: int) -> None:
         sampler.__exit__(None, None, None)
     ms = e0.elapsed_time(e1) / args.steps
     ms = reduce_max(ms, world)
+    # roofline: counted operations per frame (forward 4 per node pair and
+    # stage: min-sum 2, scale 1, g 1; reverse 7: two adjoint selects, two
+    # products, the g adjoint, the scale-gradient product and sum; 8 per
+    # information leaf: loss and seed) against the lane-op peak, and LLR plus
+    # transmitted-bit bytes against the HBM bandwidth
+    ops_frame = 11 * n * (N // 2) + 8 * K
+    bytes_frame = 4 * N + N // 8
+    peaks = measured_peaks()
+    sms = ps.polar_device_info()["sm_count"]
+    alu_peak = sms * ALU_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6
+    if ops_frame / alu_peak >= bytes_frame / (peaks["hbm_gbs"] * 1e9):
+        roof = {"bound": "alu", "achieved": ops_frame * B / (ms / 1e3) / 1e12, "peak": alu_peak / 1e12, "unit": "Top/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_frame * B / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    cpu = gsc_cpu_baseline(g, g["frames"]) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
 
     # training the scales (Adam), then the learned scales in the stack decoder
     sc = torch.ones(n, dtype=torch.float32, device="cuda", requires_grad=True)
@@ -711,8 +749,78 @@ def bench_gsc(args, rank: int, world: int, local_rank: int) -> None:
                            "scs_fer_check": {"workload": f"PC({w['N']},{w['K']}) CRC-{w['crc']} D={w['D']} "
                                                          f"L={w['L']}, {w['frames']} frames at 2.0 dB",
                                              "fer_unit_scales": fer["unit"], "fer_learned_scales": fer["learned"]}},
-                "clocks": sampler.summary() if sampler else None}
+                "roofline": roof, "cpu_baseline": cpu, "clocks": sampler.summary() if sampler else None}
         print(json.dumps(line), flush=True)
+
+
+def gsc_cpu_baseline(g, frames: int = 4096):
+    """The double-precision oracle's loss and gradient on a bounded sample of
+    the gradient workload (host-made frames), in frames/s, on all host cores."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+
+    threads = os.cpu_count() or 1
+    N, K = g["N"], g["K"]
+    fr = oracle.construct(N, K, g["design_snr_db"])
+    msg = W.message_bits(int(g["seed"]) + 77, frames, K)
+    cw = oracle.encode_batch(msg, N, K, fr, 0)
+    llr = W.bpsk_awgn_llr(cw, W.awgn_noise(int(g["seed"]) + 77, frames, N), W.sigma_from_ebn0(g["ebn0"][0], K / N))
+    u = np.zeros((frames, N), np.uint8)
+    u[:, fr == 0] = msg
+    scales = np.ones(N.bit_length() - 1)
+    parts = np.array_split(np.arange(frames), threads)
+    from concurrent.futures import ThreadPoolExecutor
+
+    def run(idx):
+        if idx.size:
+            oracle.gsc_loss_grad(llr[idx].astype(np.float64), u[idx], fr, scales)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(run, parts))
+    dt = time.perf_counter() - t0
+    return {"value": frames / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "sample": f"{frames} host-made frames, loss and gradient in double precision, wall time {dt:.2f} s "
+                      f"on {threads} host threads"}
+
+
+def mixed_cpu_baseline(frames: int, w=MIXED):
+    """The oracle on a bounded sample of the mixed workload: the first
+    `frames` (N, K, D, Eb/N0) draws, with messages, encodings and LLRs made on
+    the host per code, decoded frame by frame on all host cores."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+
+    threads = os.cpu_count() or 1
+    draw = W.mixed_frames(int(w["seed"]), frames)
+    jobs = []
+    for (N, K) in sorted(set(zip(draw["N"].tolist(), draw["K"].tolist()))):
+        sel = np.nonzero((draw["N"] == N) & (draw["K"] == K))[0]
+        fr = oracle.construct(N, K, w["design_snr_db"])
+        seed = int(w["seed"]) * 31 + N * 7 + K
+        msg = W.message_bits(seed, sel.size, K - w["crc"])
+        cw = oracle.encode_batch(msg, N, K, fr, w["crc"])
+        sig = np.array([W.sigma_from_ebn0(float(e), K / N) for e in draw["ebn0_db"][sel]])
+        llr = W.bpsk_awgn_llr(cw, W.awgn_noise(seed, sel.size, N), sig)
+        jobs += [(llr[j], N, K, fr, int(draw["D"][b])) for j, b in enumerate(sel)]
+    from concurrent.futures import ThreadPoolExecutor
+
+    def run(j):
+        llr, N, K, fr, D = j
+        oracle.scs_decode_batch(llr, N, K, fr, fast=True, D=D, L=D, crc_len=w["crc"])
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(run, jobs))
+    dt = time.perf_counter() - t0
+    bits = sum(j[2] - w["crc"] for j in jobs)
+    return {"value": bits / dt / 1e9, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {frames} draws of the mixed workload (host-made frames), decode-only wall time "
+                      f"{dt:.2f} s on {threads} host threads"}
 
 
 # ------------------------------------------------------------ served workload
