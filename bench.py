@@ -37,6 +37,15 @@ if ROOT not in sys.path:
 
 WORKLOAD = dict(N=1024, K=512, crc=16, D=32, L=32, fast=True, frames=1 << 20, ebn0=(1.5, 2.0, 2.5, 3.0), seed=2,
                 design_snr_db=0.0, systematic=False)
+# the decoder setting of the paper's experiments (Sec. 5): PC(1024,512) with
+# CRC-24C, stack depth 8192, visit cap 8, systematic encoding; the frozen set
+# comes from the Bhattacharyya construction (the paper uses the 5G sequence)
+PAPER = dict(N=1024, K=512, crc=24, D=8192, L=8, fast=True, frames=1 << 19, ebn0=(0.0, 0.5, 1.0, 1.5, 2.0, 2.5, 3.0),
+             seed=6, design_snr_db=0.0, systematic=True)
+# the paper's own FSSCS-RM figures at those points (Sec. 5, throughput and FER
+# plots): Mb/s of information bits per CPU thread on a Ryzen 5 1600, and FER
+PAPER_FSSCS_RM = dict(mbps_per_thread=(0.169, 0.182, 0.232, 0.343, 0.449, 0.620, 0.925),
+                      fer=(9.81e-1, 8.11e-1, 3.54e-1, 6.08e-2, 3.68e-3, 1.10e-4, None))
 ALU_LANES_PER_SM = 128  # FP32/INT32 lanes per SM (4 partitions x 32)
 
 
@@ -265,7 +274,7 @@ def bench_reference(args, rank: int, world: int) -> None:
 
 
 # ----------------------------------------------------------------- our arm
-def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
+def bench_ours(args, rank: int, world: int, local_rank: int, base=WORKLOAD) -> None:
     import numpy as np
     import torch
 
@@ -273,7 +282,7 @@ def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
 
     torch.cuda.set_device(local_rank)
     ps.load(build_if_missing=True)
-    w = dict(WORKLOAD, systematic=bool(args.systematic))
+    w = dict(base, systematic=bool(args.systematic) or bool(base["systematic"]))
     if args.frames:
         w["frames"] = int(args.frames)
     B, N, K, crc, D, L = w["frames"], w["N"], w["K"], w["crc"], w["D"], w["L"]
@@ -377,13 +386,22 @@ def bench_ours(args, rank: int, world: int, local_rank: int) -> None:
     clocks = sampler.summary() if sampler else None
 
     if rank == 0:
+        config = {"workload": workload_name(w), "frames_per_step_per_gpu": B * npts,
+                  "message_bits_per_frame": kmsg,
+                  "l2": f"inputs larger than L2 ({B * w['N'] * 4 / 2**30:.1f} GiB of LLRs per launch)",
+                  "parallelism": f"frames sharded over {world} GPU(s), no data-path collective",
+                  "per_point": per_point}
+        if base is PAPER:
+            config["paper_fsscs_rm_context"] = {
+                "note": "the paper's CPU figures (5G-sequence frozen set, one Ryzen 5 1600 thread); context only",
+                "per_point": [{"ebn0_db": e, "paper_mbps_per_thread": t, "paper_fer": f,
+                               "this_gpu_mbps": pp["info_gbps"] * 1e3, "this_fer": pp["fer"]}
+                              for e, t, f, pp in zip(w["ebn0"], PAPER_FSSCS_RM["mbps_per_thread"],
+                                                     PAPER_FSSCS_RM["fer"], per_point)]}
         line = {"metric": "decoded info Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload_name(w), "frames_per_step_per_gpu": B * npts,
-                           "message_bits_per_frame": kmsg, "l2": "inputs larger than L2 (4 GiB of LLRs per launch)",
-                           "parallelism": f"frames sharded over {world} GPU(s), no data-path collective",
-                           "per_point": per_point},
+                "config": config,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": npts * args.steps,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -738,6 +756,21 @@ def bench_gsc(args, rank: int, world: int, local_rank: int) -> None:
         torch.cuda.synchronize()
         fer[name] = float((info != dmsg).any(dim=1).double().mean().item())
     dplan.set_scales(None)
+    # the same scales in the plain bit-level decoder of PC(256,128), D = 16,
+    # L = 4, no CRC, at 2.5 dB: a tree of 8 stages takes the scales learned for
+    # stages 0 .. 7 (child nodes of 1 .. 128 values)
+    c1 = dict(N=256, K=128, crc=0, D=16, L=4, frames=g["fer_frames"], ebn0=(2.5,), seed=1, design_snr_db=0.0)
+    n1 = c1["N"].bit_length() - 1
+    p1 = ps.Plan(c1["N"], c1["K"], ps.polar_construct(c1["N"], c1["K"], c1["design_snr_db"]), fast_nodes=False)
+    l1, m1 = make_gpu_inputs(ps, p1, c1["frames"], rank, c1)
+    fer1 = {}
+    for name, scales in (("unit", None), ("learned", learned[:n1].copy())):
+        p1.set_scales(scales)
+        info, pm, st = ps.decode(p1, l1[0], c1["D"], c1["L"])
+        torch.cuda.synchronize()
+        fer1[name] = float((info != m1).any(dim=1).double().mean().item())
+    p1.set_scales(None)
+    del l1, m1
     if rank == 0:
         line = {"metric": "genie-aided SC forward+backward frames/s", "value": B * world / (ms / 1e3),
                 "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -748,7 +781,12 @@ def bench_gsc(args, rank: int, world: int, local_rank: int) -> None:
                            "learned_scales": [round(float(v), 5) for v in learned],
                            "scs_fer_check": {"workload": f"PC({w['N']},{w['K']}) CRC-{w['crc']} D={w['D']} "
                                                          f"L={w['L']}, {w['frames']} frames at 2.0 dB",
-                                             "fer_unit_scales": fer["unit"], "fer_learned_scales": fer["learned"]}},
+                                             "fer_unit_scales": fer["unit"], "fer_learned_scales": fer["learned"]},
+                           "plain_scs_fer_check": {"workload": f"PC({c1['N']},{c1['K']}) bit-level, no CRC, "
+                                                               f"D={c1['D']} L={c1['L']}, {c1['frames']} frames at "
+                                                               f"{c1['ebn0'][0]} dB, scales of stages 0..{n1 - 1}",
+                                                   "fer_unit_scales": fer1["unit"],
+                                                   "fer_learned_scales": fer1["learned"]}},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": sampler.summary() if sampler else None}
         print(json.dumps(line), flush=True)
 
@@ -905,7 +943,7 @@ def cpu_baseline(frames: int, w=WORKLOAD):
     threads = _os.cpu_count() or 1
     fr, msg, llrs = oracle_sample_inputs(frames, 0, w)
     dt, _ = run_oracle(fr, llrs, threads, w)
-    kmsg = WORKLOAD["K"] - WORKLOAD["crc"]
+    kmsg = w["K"] - w["crc"]
     nf = frames * len(llrs)
     return {"value": nf * kmsg / dt / 1e9, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
             "sample": f"first {frames} frames of each of the {len(llrs)} Eb/N0 points ({nf} frames), "
@@ -918,9 +956,10 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "mixed", "serve", "gsc"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "mixed", "serve", "gsc", "paper"], default="sweep",
                     help="sweep: the PC(1024,512) Eb/N0 sweep (default); mixed: the 2M-frame mixed batch; "
-                         "serve: Poisson-arrival serving; gsc: genie-aided SC gradient and learned scales")
+                         "serve: Poisson-arrival serving; gsc: genie-aided SC gradient and learned scales; "
+                         "paper: the paper's decoder setting (CRC-24C, D = 8192, L = 8) over 0-3 dB")
     ap.add_argument("--serve-rate", type=float, default=0.0, help="serve workload: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="serve workload: seconds of arrivals")
     ap.add_argument("--frames", type=int, default=0, help="frames per Eb/N0 point (default 1048576)")
@@ -953,6 +992,8 @@ def main(argv=None) -> int:
             bench_serve(args, rank, world, local_rank)
         elif args.workload == "gsc":
             bench_gsc(args, rank, world, local_rank)
+        elif args.workload == "paper":
+            bench_ours(args, rank, world, local_rank, base=PAPER)
         else:
             bench_ours(args, rank, world, local_rank)
     finally:

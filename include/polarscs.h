@@ -54,7 +54,9 @@ extern "C" {
 #define POLAR_ENOMEM (-2) /* host or device allocation failed */
 #define POLAR_ECUDA (-3)  /* a CUDA call failed (no device, launch error) */
 #define POLAR_ELIMIT (-4) /* valid code, but beyond the GPU kernel's limits:
-                             N > 8192, D > 64 or L > 255 */
+                             N > 8192, L > 255, D > 65536 (scs_decode_batch,
+                             min-sum plans) or D > 64 (the other decoders
+                             and exact-f plans) */
 #define POLAR_ESCRATCH (-5) /* scs_decode_batch_noalloc only: the plan's tables
                                exceed its 1 MiB static table area, or one
                                warp's scratch exceeds its 16 MiB static array */
@@ -64,7 +66,8 @@ extern "C" {
 
 /* Maximum sizes the GPU decoder accepts. */
 #define POLAR_MAX_N_GPU 8192
-#define POLAR_MAX_D_GPU 64
+#define POLAR_MAX_D_GPU 64          /* register stack: every decoder */
+#define POLAR_MAX_D_GPU_DEEP 65536  /* memory stack: scs_decode_batch only */
 #define POLAR_MAX_L_GPU 255
 
 /* Opaque decoding plan: the precomputed schedule of Sec. 3.1 (Fig. fsscsch)
@@ -155,6 +158,13 @@ int polar_encode(const uint8_t *msg, int N, int K, const uint8_t *frozen, int cr
  *  d_stats  device out or NULL, [B, 4] uint32: pops, path switches, counted
  *           operations (the ALU-roofline convention of the design notes),
  *           expansions.
+ * D <= 64 keeps the stack in registers.  64 < D <= POLAR_MAX_D_GPU_DEEP
+ * (e.g. the D = 8192 of Sec. 5) keeps it in per-warp scratch memory with the
+ * same search order (min-sum plans only; an exact-f plan gives POLAR_ELIMIT);
+ * that scratch holds one beta snapshot per iteration, L * (branching nodes +
+ * 9) + 3 of them, and up to min(D, 7 * iterations + 1) entries of 16 bytes,
+ * and a launch holds at most 8 GiB of it (fewer resident warps when one
+ * warp's share is large; POLAR_ELIMIT when one warp's exceeds it).
  * Scratch (the in-place beta arrays of stacked paths) is allocated
  * stream-ordered per call.  Asynchronous on stream; errors are returned
  * before launch (POLAR_EINVAL, POLAR_ELIMIT) or from the launch

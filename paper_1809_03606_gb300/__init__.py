@@ -21,6 +21,7 @@ from . import _build
 POLAR_OK, POLAR_CRC_FAIL, POLAR_TIMEOUT = 0, 1, 2
 POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ELIMIT, POLAR_ESCRATCH, POLAR_ETIMEOUT = -1, -2, -3, -4, -5, -6
 MAX_N_GPU, MAX_D_GPU, MAX_L_GPU = 8192, 64, 255
+MAX_D_GPU_DEEP = 65536  # scs_decode_batch of min-sum plans (memory stack)
 OP_NAMES = {0: "alpha", 1: "beta", 2: "R0", 3: "R1", 4: "REP", 5: "SPC", 6: "leaf0", 7: "leaf1"}
 
 EXPORTED = (

@@ -149,7 +149,8 @@ extern "C" int scs_decode_batch(const polar_plan *p, const float *d_llr, int B, 
                                 float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream) {
     if (!p || B < 0 || D < 1 || L < 1) return POLAR_EINVAL;
     if (B > 0 && (!d_llr || !d_info || !d_pm || !d_status)) return POLAR_EINVAL;
-    if (p->N > POLAR_MAX_N_GPU || D > POLAR_MAX_D_GPU || L > POLAR_MAX_L_GPU) return POLAR_ELIMIT;
+    if (p->N > POLAR_MAX_N_GPU || D > POLAR_MAX_D_GPU_DEEP || L > POLAR_MAX_L_GPU) return POLAR_ELIMIT;
+    if (D > POLAR_MAX_D_GPU && p->exact) return POLAR_ELIMIT;  // the memory stack decodes min-sum plans
     if (B == 0) return 0;
     const DeviceTables *dt = nullptr;
     int rc = plan_device(p, &dt);

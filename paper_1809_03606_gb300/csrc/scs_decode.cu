@@ -31,6 +31,7 @@
 //    optional per-stage scales of f, rounded on their own (no FMA).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -43,6 +44,7 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;  // path-metric bits of an empty slot
 constexpr uint32_t NOSNAP = 0xFFu;       // snapshot id of the initial path
+constexpr uint32_t NOSNAP_DEEP = 0xFFFFFFu;  // the same for the memory stack (24-bit slot ids)
 constexpr uint32_t FLIP_ALL = 16u;       // REP second candidate: flip every bit
 // SPC candidates (reading R8): the 8 flip masks over the four least reliable
 // positions whose parity equals the hard-decision parity, ascending, packed
@@ -65,6 +67,9 @@ struct Code {
 };
 
 constexpr int kMaxCodes = 64;  // codes of one mixed batch (shared-memory table)
+// scratch budget of one memory-stack launch (D > 64): fewer resident warps
+// when one warp's snapshots and entries are large
+constexpr long long kDeepScratchBytes = 8LL << 30;
 constexpr int kBadFrame = 3;   // status of a mixed-batch frame whose descriptor is invalid
 
 struct Args {
@@ -97,6 +102,11 @@ struct Args {
     int *error_flag;                 // device: a wait ran out
     unsigned long long wait_ns;      // longest wait for one request
     long long serve_stage_off;       // words into a warp's scratch where its LLR staging starts
+    // memory stack (D > 64): entries after the snapshots in a warp's scratch,
+    // per-block best entries after the visit counters in its shared memory
+    long long deep_ent_off;          // words into a warp's scratch
+    int deep_best_off;               // bytes into a warp's shared memory
+    int deep_cap;                    // entries the region holds
 };
 
 // Optional per-phase cycle counters (debug builds with -DPOLAR_PHASE_TIMERS):
@@ -549,6 +559,8 @@ template <int NS>
 struct Stack {
     uint32_t pm[NS], meta[NS], seq[NS], aux[NS];  // meta = len | sched << 16
 };
+template <>
+struct Stack<0> {};  // the memory stack keeps nothing in registers
 
 __device__ __forceinline__ bool slot_exists(int j, int lane, int D) { return j * 32 + lane < D; }
 
@@ -755,13 +767,177 @@ __device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int
     __syncwarp();
 }
 
+// ---- the memory stack (depths above 64, e.g. the D = 8192 of Sec. 5) ----
+// Entries {pm bits, meta, seq, aux} are dense in [0, count) of a per-warp
+// region of global scratch (aux = snapshot slot | flip mask << 24); for each
+// block of 32 entries shared memory holds {pm bits, seq} of its best entry
+// (smallest pm, ties newest), so a pop reads the block bests, then one block.
+// A popped entry's hole is filled by the last entry.  The order rules are
+// those of the register stack.
+struct MemStack {
+    uint4 *e;     // global: the entries
+    uint2 *best;  // shared: best entry per block of 32
+    int cap;      // entries the region holds
+};
+
+struct Popped {
+    uint32_t pmb, meta, aux;
+    int ok;
+};
+
+struct Worst {
+    uint32_t pm;
+    int idx;
+};
+
+// best[blk] from the block's entries below `count`
+__device__ __noinline__ void mem_block_best(MemStack ms, int blk, int count, int lane) {
+    const int i = blk * 32 + lane;
+    const uint4 v = i < count ? ms.e[i] : make_uint4(EMPTY, 0u, 0u, 0u);
+    const uint32_t gp = __reduce_min_sync(FULL, v.x);
+    const uint32_t gs = __reduce_max_sync(FULL, v.x == gp ? v.z : 0u);
+    if (lane == 0) ms.best[blk] = make_uint2(gp, gs);
+    __syncwarp();
+}
+
+// remove and return the best entry (smallest pm, ties newest); ok = 0 if
+// there is none or the block bests disagree with the entries
+__device__ __noinline__ Popped mem_pop(MemStack ms, int count, int lane) {
+    Popped r{EMPTY, 0u, 0u, 0};
+    const int nb = (count + 31) >> 5;
+    uint32_t bp = EMPTY, bs = 0u;
+    int bb = 0;
+    #pragma unroll 1
+    for (int k = lane; k < nb; k += 32) {
+        const uint2 v = ms.best[k];
+        if (v.x < bp || (v.x == bp && v.y > bs)) {
+            bp = v.x;
+            bs = v.y;
+            bb = k;
+        }
+    }
+    const uint32_t gp = __reduce_min_sync(FULL, bp);
+    if (gp == EMPTY) return r;
+    const uint32_t gs = __reduce_max_sync(FULL, bp == gp ? bs : 0u);
+    const uint32_t bal = __ballot_sync(FULL, bp == gp && bs == gs);
+    const int blk = __shfl_sync(FULL, bb, __ffs(bal) - 1);
+    const int i = blk * 32 + lane;
+    const uint4 v = i < count ? ms.e[i] : make_uint4(EMPTY, 0u, 0u, 0u);
+    const uint32_t hit = __ballot_sync(FULL, i < count && v.x == gp && v.z == gs);
+    if (!hit) return r;
+    const int wl = __ffs(hit) - 1;
+    r.pmb = gp;
+    r.meta = __shfl_sync(FULL, v.y, wl);
+    r.aux = __shfl_sync(FULL, v.w, wl);
+    const int hole = blk * 32 + wl, last = count - 1;
+    if (hole != last && lane == 0) ms.e[hole] = ms.e[last];
+    __syncwarp();
+    mem_block_best(ms, blk, last, lane);
+    const int lb = last >> 5;
+    if (lb != blk && lb * 32 < last) mem_block_best(ms, lb, last, lane);
+    r.ok = 1;
+    return r;
+}
+
+// the worst of `count` >= 1 entries: largest pm, ties oldest
+__device__ __noinline__ Worst mem_worst(MemStack ms, int count, int lane) {
+    uint32_t lw = 0u, ls = EMPTY;
+    int li = -1;
+    #pragma unroll 1
+    for (int i = lane; i < count; i += 32) {
+        const uint4 v = ms.e[i];
+        if (li < 0 || v.x > lw || (v.x == lw && v.z < ls)) {
+            lw = v.x;
+            ls = v.z;
+            li = i;
+        }
+    }
+    const uint32_t gw = __reduce_max_sync(FULL, li >= 0 ? lw : 0u);
+    const uint32_t gs = __reduce_min_sync(FULL, (li >= 0 && lw == gw) ? ls : EMPTY);
+    const uint32_t bal = __ballot_sync(FULL, li >= 0 && lw == gw && ls == gs);
+    Worst w;
+    w.pm = gw;
+    w.idx = __shfl_sync(FULL, li, __ffs(bal) - 1);
+    return w;
+}
+
+// insert candidates 0..nc-1 in order, as insert_cands does; returns the new
+// count, or -1 if the region would overflow (cannot happen with the host's
+// sizing: at most 1 + 7 entries per iteration)
+__device__ __noinline__ int mem_insert(MemStack ms, int count, const Cands c, float pm, uint32_t meta, uint32_t base,
+                                       uint32_t slot, int D, int lane) {
+    const uint32_t my_pmb = __float_as_uint(__fadd_rn(pm, c.delta(lane < c.nc ? lane : 0)));
+    const int nfree = D - count;
+    const int nb = c.nc < nfree ? c.nc : nfree;
+    if (count + nb > ms.cap) return -1;
+    if (nb > 0) {
+        if (lane < nb)
+            ms.e[count + lane] = make_uint4(my_pmb, meta, base + uint32_t(c.nc - 1 - lane), slot | (c.mask(lane) << 24));
+        __syncwarp();
+        const int b0 = count >> 5, b1 = (count + nb - 1) >> 5;
+        count += nb;
+        mem_block_best(ms, b0, count, lane);
+        if (b1 != b0) mem_block_best(ms, b1, count, lane);
+    }
+    if (nb < c.nc) {  // a full stack: strict replacement of the worst entry
+        Worst w = mem_worst(ms, count, lane);
+        uint32_t todo = __ballot_sync(FULL, lane >= nb && lane < c.nc && my_pmb < w.pm);
+        bool stale = false;
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const uint32_t pmb = __shfl_sync(FULL, my_pmb, k);
+            if (stale) {
+                w = mem_worst(ms, count, lane);
+                stale = false;
+            }
+            if (pmb < w.pm) {
+                if (lane == 0)
+                    ms.e[w.idx] = make_uint4(pmb, meta, base + uint32_t(c.nc - 1 - k), slot | (c.mask(k) << 24));
+                __syncwarp();
+                mem_block_best(ms, w.idx >> 5, count, lane);
+                stale = true;
+            }
+        }
+    }
+    return count;
+}
+
+// the L-prune: drop every entry of length <= s (order kept), rebuild the
+// block bests; returns the new count
+__device__ __noinline__ int mem_prune(MemStack ms, int count, int s, int lane) {
+    const uint32_t lt = (1u << lane) - 1u;
+    int out = 0;
+    #pragma unroll 1
+    for (int b0 = 0; b0 < count; b0 += 32) {
+        const int i = b0 + lane;
+        const uint4 v = i < count ? ms.e[i] : make_uint4(EMPTY, 0u, 0u, 0u);
+        const bool keep = i < count && int(v.y & 0xFFFFu) > s;
+        const uint32_t bal = __ballot_sync(FULL, keep);
+        __syncwarp();  // the block is read before any lane writes into it
+        if (keep) ms.e[out + __popc(bal & lt)] = v;
+        out += __popc(bal);
+    }
+    __syncwarp();
+    #pragma unroll 1
+    for (int blk = 0; blk * 32 < out; ++blk) mem_block_best(ms, blk, out, lane);
+    return out;
+}
+
+// NS = 1, 2: the register stack (D <= 32, 64); NS = 0: the memory stack `ms`
 template <int NS, bool EXACT, bool STATS>
 __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Warp &w,
-                                             unsigned b, uint32_t *orow) {
+                                             unsigned b, uint32_t *orow, const MemStack ms) {
+    constexpr bool DEEP = NS == 0;
+    constexpr uint32_t nosnap = DEEP ? NOSNAP_DEEP : NOSNAP;
+    constexpr int mask_shift = DEEP ? 24 : 8;
     const int lane = w.lane;
     const int N = c.N, W = c.W, n = c.n;
     const int SW = c.snap_words;
     const int max_iter = L * (c.nbranch + 9) + 2;
+    // snapshot slots: 0 .. D-1 reused (register stack) or one per iteration
+    // (memory stack); the slot after them keeps the first complete path
+    const int first_slot = DEEP ? max_iter : D;
     const uint32_t stack_cost = 2u * uint32_t(D > 2 ? 32 - __clz(D - 1) : 1);
 
     PT_INIT
@@ -772,25 +948,33 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
     __syncwarp();
 
     Stack<NS> st;
+    if constexpr (DEEP) {
+        if (lane == 0) {  // the initial path: pm 0, length 0, schedule 0
+            ms.e[0] = make_uint4(__float_as_uint(0.0f), 0u, 0u, NOSNAP_DEEP);
+            ms.best[0] = make_uint2(__float_as_uint(0.0f), 0u);
+        }
+        __syncwarp();
+    } else {
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-        st.pm[j] = EMPTY;
-        st.meta[j] = 0u;
-        st.seq[j] = 0u;
-        st.aux[j] = NOSNAP;
-    }
-    if (lane == 0) {  // the initial path: pm 0, length 0, schedule 0
-        st.pm[0] = __float_as_uint(0.0f);
-        st.meta[0] = 0u;
-        st.seq[0] = 0u;
-        st.aux[0] = NOSNAP;
+        for (int j = 0; j < NS; ++j) {
+            st.pm[j] = EMPTY;
+            st.meta[j] = 0u;
+            st.seq[j] = 0u;
+            st.aux[j] = NOSNAP;
+        }
+        if (lane == 0) {  // the initial path: pm 0, length 0, schedule 0
+            st.pm[0] = __float_as_uint(0.0f);
+            st.meta[0] = 0u;
+            st.seq[0] = 0u;
+            st.aux[0] = NOSNAP;
+        }
     }
     int count = 1;
     uint32_t seq_next = 1;
     uint32_t ops = stack_cost;  // counted operations (roofline convention)
     uint32_t n_iter = 0, n_switch = 0, n_exp = 0;
 
-    uint32_t cur_snap = NOSNAP;  // snapshot of the latest expansion
+    uint32_t cur_snap = nosnap;  // snapshot of the latest expansion
     bool beta_dirty = false;     // working beta replaced since that expansion
     uint32_t applied = 0;        // flips applied on top of the latest snapshot
     int cm[4] = {0, 0, 0, 0};
@@ -817,45 +1001,57 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             break;
         }
         // ---- pop the best path: smallest pm, ties to the newest ----
-        uint32_t lp = st.pm[0], ls = st.seq[0];
-        int lj = 0;
-#pragma unroll
-        for (int j = 1; j < NS; ++j)
-            if (st.pm[j] < lp || (st.pm[j] == lp && st.pm[j] != EMPTY && st.seq[j] > ls)) {
-                lp = st.pm[j];
-                ls = st.seq[j];
-                lj = j;
+        uint32_t p_pmb, p_meta, p_aux;
+        if constexpr (DEEP) {
+            const Popped pp = mem_pop(ms, count, lane);
+            if (!pp.ok) {  // count out of step with the entries: stop safely
+                status = POLAR_TIMEOUT;
+                break;
             }
-        const uint32_t gp = __reduce_min_sync(FULL, lp);
-        if (gp == EMPTY) {  // count out of step with the slots: stop safely
-            status = POLAR_TIMEOUT;
-            break;
-        }
-        const uint32_t gs = __reduce_max_sync(FULL, lp == gp ? ls : 0u);
-        const uint32_t bal = __ballot_sync(FULL, lp == gp && ls == gs);
-        const int wl = __ffs(bal) - 1;
-        const uint32_t p_pmb = gp;
-        uint32_t my_meta = st.meta[0], my_aux = st.aux[0];  // this lane's best entry
+            p_pmb = pp.pmb;
+            p_meta = pp.meta;
+            p_aux = pp.aux;
+        } else {
+            uint32_t lp = st.pm[0], ls = st.seq[0];
+            int lj = 0;
 #pragma unroll
-        for (int j = 1; j < NS; ++j)
-            if (lj == j) {
-                my_meta = st.meta[j];
-                my_aux = st.aux[j];
+            for (int j = 1; j < NS; ++j)
+                if (st.pm[j] < lp || (st.pm[j] == lp && st.pm[j] != EMPTY && st.seq[j] > ls)) {
+                    lp = st.pm[j];
+                    ls = st.seq[j];
+                    lj = j;
+                }
+            const uint32_t gp = __reduce_min_sync(FULL, lp);
+            if (gp == EMPTY) {  // count out of step with the slots: stop safely
+                status = POLAR_TIMEOUT;
+                break;
             }
-        const uint32_t p_meta = __shfl_sync(FULL, my_meta, wl);
-        const uint32_t p_aux = __shfl_sync(FULL, my_aux, wl);
-        if (lane == wl) {
+            const uint32_t gs = __reduce_max_sync(FULL, lp == gp ? ls : 0u);
+            const uint32_t bal = __ballot_sync(FULL, lp == gp && ls == gs);
+            const int wl = __ffs(bal) - 1;
+            p_pmb = gp;
+            uint32_t my_meta = st.meta[0], my_aux = st.aux[0];  // this lane's best entry
 #pragma unroll
-            for (int j = 0; j < NS; ++j)
-                if (lj == j) st.pm[j] = EMPTY;
+            for (int j = 1; j < NS; ++j)
+                if (lj == j) {
+                    my_meta = st.meta[j];
+                    my_aux = st.aux[j];
+                }
+            p_meta = __shfl_sync(FULL, my_meta, wl);
+            p_aux = __shfl_sync(FULL, my_aux, wl);
+            if (lane == wl) {
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    if (lj == j) st.pm[j] = EMPTY;
+            }
         }
         --count;
         ++n_iter;
         ops += stack_cost;
         const int p_sched = int(p_meta >> 16);
-        const uint32_t p_snap = p_aux & 0xFFu;
-        const uint32_t p_mask = (p_aux >> 8) & 0x1Fu;
-        if (p_snap != NOSNAP && p_snap >= uint32_t(D)) {  // never produced; guards the scratch index
+        const uint32_t p_snap = p_aux & nosnap;
+        const uint32_t p_mask = (p_aux >> mask_shift) & 0x1Fu;
+        if (p_snap != nosnap && p_snap >= uint32_t(first_slot)) {  // never produced; guards the scratch index
             status = POLAR_TIMEOUT;
             break;
         }
@@ -906,7 +1102,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             if (!have_first) {
                 have_first = true;
                 first_pm = __uint_as_float(p_pmb);
-                uint32_t *sp = w.scr + size_t(D) * SW;
+                uint32_t *sp = w.scr + size_t(first_slot) * SW;
                 #pragma unroll 1
                 for (int k = lane; k < W; k += 32) sp[k] = w.beta[k];
                 __syncwarp();
@@ -1018,14 +1214,18 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             __syncwarp();
             if (int(vc) >= L) {
                 ops += stack_cost;
-                int removed = 0;
+                if constexpr (DEEP) {
+                    count = mem_prune(ms, count, s, lane);
+                } else {
+                    int removed = 0;
 #pragma unroll
-                for (int j = 0; j < NS; ++j) {
-                    const bool kill = st.pm[j] != EMPTY && int(st.meta[j] & 0xFFFFu) <= s;
-                    removed += __popc(__ballot_sync(FULL, kill));
-                    if (kill) st.pm[j] = EMPTY;
+                    for (int j = 0; j < NS; ++j) {
+                        const bool kill = st.pm[j] != EMPTY && int(st.meta[j] & 0xFFFFu) <= s;
+                        removed += __popc(__ballot_sync(FULL, kill));
+                        if (kill) st.pm[j] = EMPTY;
+                    }
+                    count -= removed;
                 }
-                count -= removed;
             }
             PT(PH_PRUNE)
 
@@ -1073,7 +1273,9 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             PT(PH_NODE)
         }
 
-        const int slot = alloc_snapshot(st, D);
+        int slot;
+        if constexpr (DEEP) slot = iter;  // one slot per iteration, never reused
+        else slot = alloc_snapshot(st, D);
         if (slot < 0) break;
         write_snapshot(w, W, SW, slot, nbits, uint32_t(m[0]) | (uint32_t(m[1]) << 16),
                        uint32_t(m[2]) | (uint32_t(m[3]) << 16), node_s, snap_lam);
@@ -1089,14 +1291,22 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
         cur_lo = valid_lo = node_lam;
         PT(PH_SNAP)
         ops += uint32_t(cd.nc) * stack_cost;
-        insert_cands(st, count, cd, pm, meta, seq_next, uint32_t(slot), D, lane);
+        if constexpr (DEEP) {
+            count = mem_insert(ms, count, cd, pm, meta, seq_next, uint32_t(slot), D, lane);
+            if (count < 0) {  // the entry region is full (excluded by its sizing)
+                status = POLAR_TIMEOUT;
+                break;
+            }
+        } else {
+            insert_cands(st, count, cd, pm, meta, seq_next, uint32_t(slot), D, lane);
+        }
         seq_next += uint32_t(cd.nc);
         PT(PH_INSERT)
     }
 
     // ---- output ----
     if (out_src == 2) {
-        const uint32_t *sp = w.scr + size_t(D) * SW;
+        const uint32_t *sp = w.scr + size_t(first_slot) * SW;
         #pragma unroll 1
         for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
     } else if (out_src == 0) {
@@ -1149,11 +1359,15 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
         for (unsigned k = b0; k < b1; ++k) {
             const unsigned b = (MIXED && a.order) ? unsigned(__ldg(a.order + k)) : k;
             if (MIXED && b >= unsigned(a.B)) continue;
-            if (!MIXED) {
+            if constexpr (!MIXED) {
                 const Code &c = a.code;
                 Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                        my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
-                decode_frame<NS, EXACT, STATS>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words);
+                MemStack ms{nullptr, nullptr, 0};
+                if constexpr (NS == 0)
+                    ms = MemStack{reinterpret_cast<uint4 *>(scr + a.deep_ent_off),
+                                  reinterpret_cast<uint2 *>(my + a.deep_best_off), a.deep_cap};
+                decode_frame<NS, EXACT, STATS>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words, ms);
             } else {
                 const int4 fd = a.frames[b];
                 if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
@@ -1167,7 +1381,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const long long lo = a.llr_off[b];
                 Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
                        reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales};
-                decode_frame<NS, false, STATS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b]);
+                decode_frame<NS, false, STATS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b], MemStack{nullptr, nullptr, 0});
             }
         }
     }
@@ -1238,7 +1452,7 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
             __syncwarp();
             Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
                    my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
-            decode_frame<NS, false, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k]);
+            decode_frame<NS, false, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k], MemStack{nullptr, nullptr, 0});
         }
         if (lane == 0) {
             a.t_done[k] = global_ns();
@@ -1283,6 +1497,7 @@ const void *kernel_fn() {
 }
 
 const void *uniform_kernel(const polar_plan *p, int D, bool stats) {
+    if (D > POLAR_MAX_D_GPU) return stats ? kernel_fn<false, 0, false, true>() : kernel_fn<false, 0, false, false>();
     const bool two = D > 32;
     if (p->exact) {
         if (two) return stats ? kernel_fn<false, 2, true, true>() : kernel_fn<false, 2, true, false>();
@@ -1348,11 +1563,29 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
     a.chunk = 1;
     a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
+    int wpb_pref = 4;
+    long long deep_fit = 0;
+    if (D > POLAR_MAX_D_GPU) {  // the memory stack
+        if (p->exact) return POLAR_ELIMIT;
+        // one snapshot slot per iteration plus the first complete path; at
+        // most 1 + 7 live entries per iteration (a pop, then <= 8 candidates)
+        const long long max_iter = (long long)L * (p->nbranch + 9) + 2;
+        const long long cap = std::min<long long>(D, 1 + 7 * max_iter);
+        a.deep_cap = int(cap);
+        a.deep_ent_off = (max_iter + 1) * a.code.snap_words;  // a multiple of 8 words: 16-byte aligned
+        a.scratch_stride = a.deep_ent_off + 4 * cap;
+        a.deep_best_off = a.warp_smem;
+        a.warp_smem = (a.warp_smem + 8 * int((cap + 31) / 32) + 15) & ~15;
+        deep_fit = kDeepScratchBytes / (a.scratch_stride * 4);  // warps whose scratch fits the budget
+        if (deep_fit < 1) return POLAR_ELIMIT;
+        while (wpb_pref > 1 && wpb_pref > deep_fit) wpb_pref >>= 1;
+    }
 
     int grid = 0, wpb = 0, smem = 0;
     const void *fn = uniform_kernel(p, D, d_stats != nullptr);
-    int rc = launch_shape(fn, false, a.warp_smem, B, 4, &grid, &wpb, &smem);
+    int rc = launch_shape(fn, false, a.warp_smem, B, wpb_pref, &grid, &wpb, &smem);
     if (rc) return rc;
+    if (deep_fit > 0 && (long long)grid * wpb > deep_fit) grid = int(deep_fit / wpb);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);

@@ -98,7 +98,11 @@ def test_decode_batch_validates_before_device_work(lib):
     assert lib.scs_decode_batch(h, dummy, 4, 0, 4, dummy, dummy, dummy, None, None) == ps.POLAR_EINVAL
     assert lib.scs_decode_batch(h, dummy, 4, 4, 0, dummy, dummy, dummy, None, None) == ps.POLAR_EINVAL
     assert lib.scs_decode_batch(h, None, 4, 4, 4, dummy, dummy, dummy, None, None) == ps.POLAR_EINVAL
-    assert lib.scs_decode_batch(h, dummy, 4, 65, 4, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
+    assert lib.scs_decode_batch(h, dummy, 4, ps.MAX_D_GPU_DEEP + 1, 4, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
+    # D > 64 needs the memory stack: the uniform decoder of a min-sum plan only
+    assert lib.scs_decode_batch_noalloc(h, dummy, 4, 65, 4, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
+    ex = ps.Plan(64, 32, fr, fast_nodes=False, exact=True)
+    assert lib.scs_decode_batch(ex.handle, dummy, 4, 65, 4, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
     assert lib.scs_decode_batch(h, dummy, 4, 8, 256, dummy, dummy, dummy, None, None) == ps.POLAR_ELIMIT
     assert lib.scs_decode_batch(h, dummy, 0, 8, 8, None, None, None, None, None) == 0  # empty batch: no-op
     big = ps.Plan(16384, 8192, ps.polar_construct(16384, 8192, 0.0))
