@@ -12,9 +12,12 @@
 //
 // GB300 mapping: one CTA per frame (persistent), the whole tree ((n+1) x N
 // values, stage lambda at offset lambda * N) in shared memory.  Stages are
-// computed layer by layer with every thread owning node pairs; the reverse
-// pass overwrites the stage values with their adjoints in place (a thread
-// reads and then writes the same two parent positions).  Per-frame sums go to
+// computed layer by layer with every thread owning node pairs: the wide top
+// stages by the whole block (a block barrier per stage), the stages whose
+// nodes fit in one warp's segment of N/8 positions by that warp alone (warp
+// synchronisation only); the reverse pass overwrites the stage values with
+// their adjoints in place (a thread reads and then writes the same two parent
+// positions).  Per-frame sums go to
 // a [B, n+1] buffer that a second kernel reduces over frames in a fixed order,
 // so results do not depend on scheduling; inside a frame each warp reduces its
 // share by a shuffle tree and the warps' sums are added in warp order once per
@@ -62,50 +65,67 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-template <typename T>
+// LOGN > 0: the code length 2^LOGN fixed at compile time (every index shift
+// and trip count a constant); LOGN = 0: any length
+template <typename T, int LOGN>
 __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
     extern __shared__ __align__(16) unsigned char gsm[];
+    const int N = LOGN ? (1 << LOGN) : a.N, n = LOGN ? LOGN : a.n, W = LOGN ? ((N + 31) >> 5) : a.W;
+    const int half = N >> 1;
     T *tree = reinterpret_cast<T *>(gsm);                           // (n+1) * N
-    uint32_t *xs = reinterpret_cast<uint32_t *>(tree + (a.n + 1) * a.N);  // (n+1) * W partial sums
+    uint32_t *xs = reinterpret_cast<uint32_t *>(tree + (n + 1) * N);  // (n+1) * W partial sums
     // per-warp partial sums of the frame's loss and of d/ds_lambda, reduced
-    // over the warps once per frame (same fixed order as a block-wide sum)
+    // over the warps once per frame in warp order
     constexpr int kWarps = kGscThreads / 32;
     __shared__ T wsum[16 * kWarps];
-    const int N = a.N, n = a.n, W = a.W, half = N >> 1;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // warp w owns positions [w seg, (w+1) seg) of every stage; a stage whose
+    // parent nodes fit in a segment (2^(lambda+1) <= seg) is updated by each
+    // warp on its own segment (its seg/2 node pairs), with warp-level
+    // synchronisation only; wider stages are shared by the block
+    const int seg = N / kWarps, pseg = seg >> 1;
+    const int lam_loc = seg >= 2 ? (30 - __clz(seg)) : -1;  // highest warp-local stage
     for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
         const T *l = a.llr + size_t(b) * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) tree[size_t(n) * N + i] = l[i];
-        // partial sums: xs[lambda] = u after the encoder stages of distance 1 .. 2^(lambda-1)
-        for (int k = threadIdx.x; k < W; k += blockDim.x) xs[k] = a.u[size_t(b) * W + k];
-        __syncthreads();
-        for (int lam = 0; lam < n; ++lam) {
-            const uint32_t *src = xs + lam * W;
-            uint32_t *dst = xs + (lam + 1) * W;
-            const int d = 1 << lam;
-            for (int k = threadIdx.x; k < W; k += blockDim.x) {
-                uint32_t x = src[k];
-                if (d < 32) {
-                    const uint32_t M = d == 1 ? 0x55555555u : d == 2 ? 0x33333333u : d == 4 ? 0x0F0F0F0Fu
-                                     : d == 8 ? 0x00FF00FFu : 0x0000FFFFu;
-                    x ^= (x >> d) & M;
-                    if (N < 32) x &= (1u << N) - 1u;
-                } else {
-                    const int dw = d >> 5;
-                    if (!(k & dw)) x ^= src[k + dw];
+        for (int i = tid; i < N; i += blockDim.x) tree[size_t(n) * N + i] = l[i];
+        // partial sums (warp 0): xs[lambda] = u after the encoder stages of
+        // distance 1 .. 2^(lambda-1)
+        if (wid == 0) {
+            for (int k = lane; k < W; k += 32) xs[k] = a.u[size_t(b) * W + k];
+            __syncwarp();
+            for (int lam = 0; lam < n; ++lam) {
+                const uint32_t *src = xs + lam * W;
+                uint32_t *dst = xs + (lam + 1) * W;
+                const int d = 1 << lam;
+                for (int k = lane; k < W; k += 32) {
+                    uint32_t x = src[k];
+                    if (d < 32) {
+                        const uint32_t M = d == 1 ? 0x55555555u : d == 2 ? 0x33333333u : d == 4 ? 0x0F0F0F0Fu
+                                         : d == 8 ? 0x00FF00FFu : 0x0000FFFFu;
+                        x ^= (x >> d) & M;
+                        if (N < 32) x &= (1u << N) - 1u;
+                    } else {
+                        const int dw = d >> 5;
+                        if (!(k & dw)) x ^= src[k + dw];
+                    }
+                    dst[k] = x;
                 }
-                dst[k] = x;
+                __syncwarp();
             }
-            __syncthreads();
         }
+        __syncthreads();
         // forward, stage n-1 down to 0
+#pragma unroll
         for (int lam = n - 1; lam >= 0; --lam) {
+            const bool loc = lam <= lam_loc;
+            const int i0 = loc ? wid * pseg + lane : tid, i1 = loc ? (wid + 1) * pseg : half;
+            const int st = loc ? 32 : int(blockDim.x);
             const int len = 1 << lam;
             const T s = a.scales[lam];
             const T *par = tree + size_t(lam + 1) * N;
             T *cur = tree + size_t(lam) * N;
             const uint32_t *bx = xs + lam * W;
-            for (int i = threadIdx.x; i < half; i += blockDim.x) {
+            for (int i = i0; i < i1; i += st) {
                 const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
                 const T x = par[ps + j], y = par[ps + len + j];
                 const int pos = ps + j;  // the left child's true bits
@@ -113,11 +133,14 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
                 cur[ps + j] = s * f_ms(x, y);
                 cur[ps + len + j] = beta ? y - x : y + x;
             }
-            __syncthreads();
+            if (loc) __syncwarp();  // the next stage reads this warp's segment only
+            else __syncthreads();
         }
-        // leaves: loss terms and the adjoint seeds (in place of the leaf values)
+        // leaves (each warp on its segment when stage 0 is warp-local): loss
+        // terms and the adjoint seeds in place of the leaf values
+        const bool loc0 = lam_loc >= 0;
         T loss = T(0);
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        for (int i = loc0 ? wid * seg + lane : tid; i < (loc0 ? (wid + 1) * seg : N); i += loc0 ? 32 : int(blockDim.x)) {
             const T L = tree[i];
             if (a.leaf_out) a.leaf_out[size_t(b) * N + i] = L;
             T adj = T(0);
@@ -132,15 +155,20 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
         loss = warp_sum(loss);
         if (lane == 0) wsum[wid] = loss;
         if (a.with_grad) {
-            __syncthreads();
+            if (loc0) __syncwarp();
+            else __syncthreads();
+#pragma unroll
             for (int lam = 0; lam < n; ++lam) {
+                const bool loc = lam <= lam_loc;
+                const int i0 = loc ? wid * pseg + lane : tid, i1 = loc ? (wid + 1) * pseg : half;
+                const int st = loc ? 32 : int(blockDim.x);
                 const int len = 1 << lam;
                 const T s = a.scales[lam];
                 T *par = tree + size_t(lam + 1) * N;
                 const T *cur = tree + size_t(lam) * N;
                 const uint32_t *bx = xs + lam * W;
                 T gs = T(0);
-                for (int i = threadIdx.x; i < half; i += blockDim.x) {
+                for (int i = i0; i < i1; i += st) {
                     const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
                     const T x = par[ps + j], y = par[ps + len + j];
                     const T gl = cur[ps + j], gr = cur[ps + len + j];
@@ -156,17 +184,18 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
                 }
                 gs = warp_sum(gs);
                 if (lane == 0) wsum[(1 + lam) * kWarps + wid] = gs;
-                __syncthreads();
+                if (lam + 1 <= lam_loc) __syncwarp();  // the next stage is this warp's too
+                else __syncthreads();
             }
             if (a.grad_llr)
-                for (int i = threadIdx.x; i < N; i += blockDim.x) a.grad_llr[size_t(b) * N + i] = tree[size_t(n) * N + i];
+                for (int i = tid; i < N; i += blockDim.x) a.grad_llr[size_t(b) * N + i] = tree[size_t(n) * N + i];
         }
         __syncthreads();
         const int nq = a.with_grad ? n + 1 : 1;
-        if (int(threadIdx.x) < nq) {
+        if (tid < nq) {
             T sum = T(0);
-            for (int i = 0; i < kWarps; ++i) sum += wsum[threadIdx.x * kWarps + i];
-            a.frame_sums[size_t(b) * (n + 1) + threadIdx.x] = sum;
+            for (int i = 0; i < kWarps; ++i) sum += wsum[tid * kWarps + i];
+            a.frame_sums[size_t(b) * (n + 1) + tid] = sum;
         }
         __syncthreads();
     }
@@ -209,10 +238,11 @@ int launch_gsc(const polar_plan *p, const uint8_t *d_info_mask, const T *d_llr, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem + int(33 * sizeof(T)) > max_smem) return POLAR_ELIMIT;
-    e = cudaFuncSetAttribute(gsc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    void (*kern)(GscArgs<T>) = N == 1024 ? gsc_kernel<T, 10> : gsc_kernel<T, 0>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gsc_kernel<T>, kGscThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGscThreads, smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return POLAR_ELIMIT;
     long long grid = (long long)sms * per_sm;
@@ -226,7 +256,7 @@ int launch_gsc(const polar_plan *p, const uint8_t *d_info_mask, const T *d_llr, 
     T *red = sums + size_t(B) * Q;
     const bool grad = d_grad_scales != nullptr || d_grad_llr != nullptr;
     GscArgs<T> a{d_llr, d_u, d_info_mask, d_scales, B, N, n, W, grad ? 1 : 0, sums, d_grad_llr, d_leaf};
-    gsc_kernel<T><<<unsigned(grid), kGscThreads, size_t(smem), stream>>>(a);
+    kern<<<unsigned(grid), kGscThreads, size_t(smem), stream>>>(a);
     e = cudaGetLastError();
     int K = 0;
     for (int i = 0; i < N; ++i) K += p->frozen[size_t(i)] ? 0 : 1;
