@@ -14,7 +14,9 @@
 //    D <= 32 and two for D <= 64: path metric bits, length|schedule
 //    position, sequence number and a reference to a beta snapshot plus a
 //    flip mask.  Pop, worst-entry search and the L-prune are warp reductions
-//    (redux.sync).
+//    (redux.sync).  Deeper stacks (up to 65536 entries, e.g. D = 8192 of
+//    Sec. 5) keep the same records in per-warp scratch memory with the best
+//    entry of every block of 32 in shared memory (MemStack below).
 //  - Each branching node writes ONE snapshot of the beta array (the hard
 //    decisions of the node in place) to scratch global memory; its 2-8
 //    candidates differ from it by flips of at most 4 positions (or all
