@@ -58,6 +58,25 @@ __device__ __forceinline__ T softplus(T z) {
     return z > T(0) ? z + log1p(exp(-z)) : log1p(exp(z));
 }
 
+// one node pair forward: left child s * f(x, y), right child y + (1 - 2 beta) x
+template <typename T>
+__device__ __forceinline__ void fwd_pair(T x, T y, uint32_t beta, T s, T &l, T &r) {
+    l = s * f_ms(x, y);
+    r = beta ? y - x : y + x;
+}
+
+// one node pair in reverse: adjoints gl, gr of the children give those of
+// the parents (ax, ay) and the pair's share of d/ds
+template <typename T>
+__device__ __forceinline__ void bwd_pair(T x, T y, T gl, T gr, uint32_t beta, T s, T &gs, T &ax, T &ay) {
+    gs += gl * f_ms(x, y);
+    const T sx = x < T(0) ? T(-1) : T(1), sy = y < T(0) ? T(-1) : T(1);
+    ax = beta ? -gr : gr;
+    ay = gr;
+    if (fabs(x) <= fabs(y)) ax += gl * s * sy;  // f = s * sgn(y) * x
+    else ay += gl * s * sx;                     // f = s * sgn(x) * y
+}
+
 // warp sum by a shuffle tree (the full sum ends in lane 0)
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -85,9 +104,36 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
     // synchronisation only; wider stages are shared by the block
     const int seg = N / kWarps, pseg = seg >> 1;
     const int lam_loc = seg >= 2 ? (30 - __clz(seg)) : -1;  // highest warp-local stage
+    // float and 128-position segments: stages 0 and 1 take 4 positions per
+    // lane, the others two adjacent node pairs per thread (each thread's one
+    // share of the warp's 64 or the block's 512 pairs)
+    constexpr bool kVec = sizeof(T) == 4 && LOGN == 10 && kGscThreads == 256;
+    // the specialised kernel loads the next frame's LLR row into registers
+    // while the current frame is computed (N / 256 values per thread)
+    constexpr int kPre = LOGN ? ((1 << LOGN) + kGscThreads - 1) / kGscThreads : 1;
+    T pre[kPre];
+    if (LOGN && int(blockIdx.x) < a.B) {
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) {
+            const int i = tid + q * kGscThreads;
+            if (i < N) pre[q] = a.llr[size_t(blockIdx.x) * N + i];
+        }
+    }
     for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
-        const T *l = a.llr + size_t(b) * N;
-        for (int i = tid; i < N; i += blockDim.x) tree[size_t(n) * N + i] = l[i];
+        if (LOGN) {
+            const int bn = b + int(gridDim.x);
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                const int i = tid + q * kGscThreads;
+                if (i < N) {
+                    tree[size_t(n) * N + i] = pre[q];
+                    if (bn < a.B) pre[q] = a.llr[size_t(bn) * N + i];
+                }
+            }
+        } else {
+            const T *l = a.llr + size_t(b) * N;
+            for (int i = tid; i < N; i += blockDim.x) tree[size_t(n) * N + i] = l[i];
+        }
         // partial sums (warp 0): xs[lambda] = u after the encoder stages of
         // distance 1 .. 2^(lambda-1)
         if (wid == 0) {
@@ -125,13 +171,43 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
             const T *par = tree + size_t(lam + 1) * N;
             T *cur = tree + size_t(lam) * N;
             const uint32_t *bx = xs + lam * W;
-            for (int i = i0; i < i1; i += st) {
-                const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
-                const T x = par[ps + j], y = par[ps + len + j];
-                const int pos = ps + j;  // the left child's true bits
-                const uint32_t beta = (bx[pos >> 5] >> (pos & 31)) & 1u;
-                cur[ps + j] = s * f_ms(x, y);
-                cur[ps + len + j] = beta ? y - x : y + x;
+            bool done = false;
+            if constexpr (kVec) {
+                if (lam <= 1) {  // two node pairs per lane in one 16-byte access
+                const int p = wid * seg + 4 * lane;
+                const float4 v = *reinterpret_cast<const float4 *>(par + p);
+                const uint32_t w = bx[p >> 5] >> (p & 31);
+                float4 o;
+                if (lam == 0) {  // pairs (p, p+1), (p+2, p+3)
+                    fwd_pair<T>(v.x, v.y, w & 1u, s, o.x, o.y);
+                    fwd_pair<T>(v.z, v.w, (w >> 2) & 1u, s, o.z, o.w);
+                } else {  // pairs (p, p+2), (p+1, p+3)
+                    fwd_pair<T>(v.x, v.z, w & 1u, s, o.x, o.z);
+                    fwd_pair<T>(v.y, v.w, (w >> 1) & 1u, s, o.y, o.w);
+                }
+                *reinterpret_cast<float4 *>(cur + p) = o;
+                done = true;
+                } else {  // two adjacent node pairs per thread in 8-byte accesses
+                    const int i = 2 * (loc ? wid * 32 + lane : tid);
+                    const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
+                    const float2 x = *reinterpret_cast<const float2 *>(par + ps + j);
+                    const float2 y = *reinterpret_cast<const float2 *>(par + ps + len + j);
+                    const uint32_t w = bx[(ps + j) >> 5] >> ((ps + j) & 31);
+                    float2 l, r;
+                    fwd_pair<T>(x.x, y.x, w & 1u, s, l.x, r.x);
+                    fwd_pair<T>(x.y, y.y, (w >> 1) & 1u, s, l.y, r.y);
+                    *reinterpret_cast<float2 *>(cur + ps + j) = l;
+                    *reinterpret_cast<float2 *>(cur + ps + len + j) = r;
+                    done = true;
+                }
+            }
+            if (!done) {
+                for (int i = i0; i < i1; i += st) {
+                    const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
+                    const int pos = ps + j;  // the left child's true bits
+                    const uint32_t beta = (bx[pos >> 5] >> (pos & 31)) & 1u;
+                    fwd_pair<T>(par[ps + j], par[ps + len + j], beta, s, cur[ps + j], cur[ps + len + j]);
+                }
             }
             if (loc) __syncwarp();  // the next stage reads this warp's segment only
             else __syncthreads();
@@ -168,19 +244,49 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
                 const T *cur = tree + size_t(lam) * N;
                 const uint32_t *bx = xs + lam * W;
                 T gs = T(0);
-                for (int i = i0; i < i1; i += st) {
-                    const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
-                    const T x = par[ps + j], y = par[ps + len + j];
-                    const T gl = cur[ps + j], gr = cur[ps + len + j];
-                    const int pos = ps + j;
-                    const uint32_t beta = (bx[pos >> 5] >> (pos & 31)) & 1u;
-                    gs += gl * f_ms(x, y);
-                    const T sx = x < T(0) ? T(-1) : T(1), sy = y < T(0) ? T(-1) : T(1);
-                    T ax = beta ? -gr : gr, ay = gr;
-                    if (fabs(x) <= fabs(y)) ax += gl * s * sy;  // f = s * sgn(y) * x
-                    else ay += gl * s * sx;                     // f = s * sgn(x) * y
-                    par[ps + j] = ax;
-                    par[ps + len + j] = ay;
+                bool done = false;
+                if constexpr (kVec) {
+                    if (lam <= 1) {  // two node pairs per lane in 16-byte accesses
+                    const int p = wid * seg + 4 * lane;
+                    const float4 v = *reinterpret_cast<const float4 *>(par + p);
+                    const float4 c = *reinterpret_cast<const float4 *>(cur + p);
+                    const uint32_t w = bx[p >> 5] >> (p & 31);
+                    float4 o;
+                    if (lam == 0) {
+                        bwd_pair<T>(v.x, v.y, c.x, c.y, w & 1u, s, gs, o.x, o.y);
+                        bwd_pair<T>(v.z, v.w, c.z, c.w, (w >> 2) & 1u, s, gs, o.z, o.w);
+                    } else {
+                        bwd_pair<T>(v.x, v.z, c.x, c.z, w & 1u, s, gs, o.x, o.z);
+                        bwd_pair<T>(v.y, v.w, c.y, c.w, (w >> 1) & 1u, s, gs, o.y, o.w);
+                    }
+                    *reinterpret_cast<float4 *>(par + p) = o;
+                    done = true;
+                    } else {  // two adjacent node pairs per thread in 8-byte accesses
+                        const int i = 2 * (loc ? wid * 32 + lane : tid);
+                        const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
+                        const float2 x = *reinterpret_cast<const float2 *>(par + ps + j);
+                        const float2 y = *reinterpret_cast<const float2 *>(par + ps + len + j);
+                        const float2 gl = *reinterpret_cast<const float2 *>(cur + ps + j);
+                        const float2 gr = *reinterpret_cast<const float2 *>(cur + ps + len + j);
+                        const uint32_t w = bx[(ps + j) >> 5] >> ((ps + j) & 31);
+                        float2 ax, ay;
+                        bwd_pair<T>(x.x, y.x, gl.x, gr.x, w & 1u, s, gs, ax.x, ay.x);
+                        bwd_pair<T>(x.y, y.y, gl.y, gr.y, (w >> 1) & 1u, s, gs, ax.y, ay.y);
+                        *reinterpret_cast<float2 *>(par + ps + j) = ax;
+                        *reinterpret_cast<float2 *>(par + ps + len + j) = ay;
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    for (int i = i0; i < i1; i += st) {
+                        const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
+                        const int pos = ps + j;
+                        const uint32_t beta = (bx[pos >> 5] >> (pos & 31)) & 1u;
+                        T ax, ay;
+                        bwd_pair<T>(par[ps + j], par[ps + len + j], cur[ps + j], cur[ps + len + j], beta, s, gs, ax, ay);
+                        par[ps + j] = ax;
+                        par[ps + len + j] = ay;
+                    }
                 }
                 gs = warp_sum(gs);
                 if (lane == 0) wsum[(1 + lam) * kWarps + wid] = gs;
