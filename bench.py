@@ -75,19 +75,23 @@ def measured_peaks() -> dict:
         return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
 
-def profiled_traffic(kernel_src: str, ebn0s) -> list[float] | None:
-    """DRAM bytes per frame at each Eb/N0 point from the committed ncu summary,
-    if it was taken on the current kernel source (its sha256 is recorded in
-    the summary) and covers every point; else None."""
+def profiled_values(kernel_src: str, key: str, ebn0s) -> list[float] | None:
+    """Per-Eb/N0 values (DRAM bytes per frame, issue-slot utilisation) from the
+    committed ncu summary, if it was taken on the current kernel source (its
+    sha256 is recorded in the summary) and covers every point; else None."""
     path = os.path.join(ROOT, "profiles", "scs_decode_pc1024_traffic.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
         if kv.get("kernel_sha256") != sha:
             return None
-        return [float(kv[f"dram_bytes_per_frame_{e}"]) for e in ebn0s]
+        return [float(kv[f"{key}_{e}"]) for e in ebn0s]
     except Exception:
         return None
+
+
+def profiled_traffic(kernel_src: str, ebn0s) -> list[float] | None:
+    return profiled_values(kernel_src, "dram_bytes_per_frame", ebn0s)
 
 
 def reduce_max(value: float, world: int) -> float:
@@ -368,6 +372,11 @@ def bench_ours(args, rank: int, world: int, local_rank: int, base=WORKLOAD) -> N
     roof["traffic"] = None if traffic_pf is None else float(sum(traffic_pf)) * B / npts
     roof["peak_source"] = (f"{peaks['source']}: {sms} SMs x {ALU_LANES_PER_SM} lanes x {peaks['sm_max_mhz']:.0f} MHz"
                            if roof["bound"] == "alu" else f"{peaks['source']} HBM copy bandwidth")
+    # what bounds the kernel in practice: its own instruction issue (ncu,
+    # same kernel source), next to the lane-op fraction above
+    issue = profiled_values(os.path.join(ROOT, "paper_1809_03606_gb300", "csrc", "scs_decode.cu"), "issue_active_pct",
+                            w["ebn0"])
+    roof["issue_slots_busy"] = None if issue is None else statistics.mean(issue) / 100.0
     per_point = []
     for p, e in enumerate(w["ebn0"]):
         ms = statistics.mean(launch_ms[k][p] for k in range(args.steps))
