@@ -145,3 +145,23 @@ def test_gpu_deep_stack_empty_and_single_frames(oracle_lib):
         m_g, pm_g, st_g, _ = _gpu(N, K, fr, llr[b:b + 1], True, 8192, 8, crc)
         m_o, pm_o, st_o, _ = oracle_lib.scs_decode_batch(llr[b:b + 1], N, K, fr, fast=True, D=8192, L=8, crc_len=crc)
         assert np.array_equal(m_o, m_g) and pm_o.view(np.uint32)[0] == pm_g.view(np.uint32)[0] and st_o[0] == st_g[0]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("N,K,crc,D,L,ebn0,B", [
+    (1024, 512, 24, 65536, 8, 1.0, 32),      # the largest depth
+    (8192, 4096, 16, 65536, 255, 3.0, 8),    # the longest code, largest depth and cap: 90 MB of scratch per
+                                             # warp, so the 8 GiB budget leaves fewer than 100 resident warps
+])
+def test_gpu_deep_stack_limits(oracle_lib, N, K, crc, D, L, ebn0, B):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ps.load(build_if_missing=True)
+    fr, llr = _frames(oracle_lib, N, K, crc, B, ebn0, seed=N + D + L)
+    m_o, pm_o, st_o, stats_o = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=True, D=D, L=L, crc_len=crc, threads=2)
+    m_g, pm_g, st_g, stats_g = _gpu(N, K, fr, llr, True, D, L, crc)
+    assert np.array_equal(m_o, m_g)
+    assert np.array_equal(pm_o.view(np.uint32), pm_g.view(np.uint32))
+    assert np.array_equal(st_o, st_g)
+    assert np.array_equal(stats_o.astype(np.uint32), stats_g)
