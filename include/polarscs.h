@@ -311,7 +311,9 @@ int polar_serve_baseline(const polar_plan_set *set, const int32_t *req, const do
 
 /* Decode one frame held in host memory (synchronous), fast nodes on:
  * llr N floats in, info_out K - crc bytes (one bit per byte) out, *pm_out the
- * final path metric.  Returns the frame status (>= 0) or an error (< 0). */
+ * final path metric.  Runs scs_decode_batch on the current device, so D may be
+ * up to POLAR_MAX_D_GPU_DEEP.  Returns the frame status (>= 0) or an error
+ * (< 0). */
 int scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int D, int L, int crc, uint8_t *info_out,
                float *pm_out);
 
