@@ -737,6 +737,14 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
 // left the stack, so at most D - 1 snapshots are referenced)
 template <int NS>
 __device__ __forceinline__ int alloc_snapshot(const Stack<NS> &st, int D) {
+    if constexpr (NS == 1) {  // D <= 32: slot ids below 32, one word
+        uint32_t used = 0u;
+        const uint32_t sn = st.aux[0] & 0xFFu;
+        if (st.pm[0] != EMPTY && sn < 32u) used = 1u << sn;
+        used = __reduce_or_sync(FULL, used);
+        const uint32_t fr = ~used & (D >= 32 ? FULL : ((1u << D) - 1u));
+        return fr ? (__ffs(int(fr)) - 1) : -1;
+    }
     uint32_t lo = 0u, hi = 0u;
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
