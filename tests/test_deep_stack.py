@@ -165,3 +165,30 @@ def test_gpu_deep_stack_limits(oracle_lib, N, K, crc, D, L, ebn0, B):
     assert np.array_equal(pm_o.view(np.uint32), pm_g.view(np.uint32))
     assert np.array_equal(st_o, st_g)
     assert np.array_equal(stats_o.astype(np.uint32), stats_g)
+
+
+@pytest.mark.gpu
+def test_gpu_paper_setting_full_size_launch(oracle_lib):
+    """The paper-setting bench's launch: 524,288 frames of systematic
+    PC(1024,512) CRC-24C, D = 8192, L = 8, at 0 dB (its hardest point), in one
+    scs_decode_batch call.  The batch tiles 2,048 host-made frames 256 times,
+    so every output has an oracle value (that of its row modulo 2,048)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ps.load(build_if_missing=True)
+    N, K, crc, D, L, base = 1024, 512, 24, 8192, 8, 2048
+    fr = oracle_lib.construct(N, K, 0.0)
+    msg = W.message_bits(606, base, K - crc)
+    cw = oracle_lib.encode_batch(msg, N, K, fr, crc, systematic=True)
+    llr = W.bpsk_awgn_llr(cw, W.awgn_noise(606, base, N), W.sigma_from_ebn0(0.0, K / N))
+    m_o, pm_o, st_o, _ = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=True, D=D, L=L, crc_len=crc, threads=8,
+                                                      systematic=True)
+    plan = ps.Plan(N, K, fr, fast_nodes=True, crc=crc, systematic=True)
+    x = torch.from_numpy(llr).cuda().repeat(256, 1)
+    info, pm, st = ps.decode(plan, x, D, L)
+    torch.cuda.synchronize()
+    del x
+    assert torch.equal(info, torch.from_numpy(ps.pack_bits(m_o)).cuda().repeat(256, 1))
+    assert torch.equal(pm.view(torch.int32), torch.from_numpy(pm_o.view(np.int32)).cuda().repeat(256))
+    assert torch.equal(st, torch.from_numpy(st_o).cuda().repeat(256))
