@@ -192,3 +192,32 @@ def test_gpu_paper_setting_full_size_launch(oracle_lib):
     assert torch.equal(info, torch.from_numpy(ps.pack_bits(m_o)).cuda().repeat(256, 1))
     assert torch.equal(pm.view(torch.int32), torch.from_numpy(pm_o.view(np.int32)).cuda().repeat(256))
     assert torch.equal(st, torch.from_numpy(st_o).cuda().repeat(256))
+
+
+@pytest.mark.gpu
+def test_gpu_deep_stack_scaled_and_host_call(oracle_lib):
+    """The memory stack with per-stage f scales (against the oracle's scaled
+    decoder), and the host single-frame call at the paper's depth."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ps.load(build_if_missing=True)
+    N, K, crc, D, L = 512, 256, 16, 500, 6
+    fr, llr = _frames(oracle_lib, N, K, crc, 400, 1.0, seed=91)
+    scales = np.random.default_rng(9).uniform(0.55, 1.25, 9).astype(np.float32)
+    plan = ps.Plan(N, K, fr, fast_nodes=True, crc=crc)
+    plan.set_scales(scales)
+    info, pm, st, stats = ps.decode(plan, torch.from_numpy(llr).cuda(), D, L, with_stats=True)
+    torch.cuda.synchronize()
+    m_o, pm_o, st_o, stats_o = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=True, D=D, L=L, crc_len=crc, threads=8,
+                                                           scales=scales)
+    assert np.array_equal(ps.unpack_bits(info.cpu().numpy(), K - crc), m_o)
+    assert np.array_equal(pm.cpu().numpy().view(np.uint32), pm_o.view(np.uint32))
+    assert np.array_equal(st.cpu().numpy(), st_o)
+    assert np.array_equal(stats.cpu().numpy().view(np.uint32), stats_o.astype(np.uint32))
+    N, K, crc = 1024, 512, 24
+    fr, llr = _frames(oracle_lib, N, K, crc, 6, 1.0, seed=92)
+    for b in range(6):
+        st1, m1, pm1 = ps.scs_decode(llr[b], N, K, fr, 8192, 8, crc)
+        st_o1, m_o1, pm_o1, _, _ = oracle_lib.scs_decode(llr[b], N, K, fr, fast=True, D=8192, L=8, crc_len=crc)
+        assert st1 == st_o1 and np.array_equal(m1, m_o1) and pm1.view(np.uint32) == pm_o1.view(np.uint32)
