@@ -82,3 +82,29 @@ def test_deterministic_and_training_reduces_loss(oracle_lib):
         first = loss.item() if first is None else first
     final = ps.genie_sc_loss(x, s, uw, plan).item()
     assert final < first
+
+
+def test_llr_gradient_at_n1024(oracle_lib):
+    """d loss / d llr at N = 1024, where the float kernel takes its vector
+    paths: central differences of the double-precision loss at a few entries
+    pin the double gradient, and the float gradient agrees with it."""
+    B, N, K = 64, 1024, 512
+    fr, plan, llr, u, uw = _problem(oracle_lib, N, K, B, 2.0, seed=17)
+    scales = np.random.default_rng(17).uniform(0.6, 1.2, 10)
+    x64 = torch.from_numpy(llr.astype(np.float64)).cuda()
+    s64 = torch.from_numpy(scales).cuda()
+    _, _, gl64 = ps.gsc_loss_grad(plan, x64, uw, s64, want_llr_grad=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(18)
+    h = 1e-7  # the loss is piecewise smooth: a small step rarely crosses a min-sum kink
+    for b, i in zip(rng.integers(0, B, 8), rng.integers(0, N, 8)):
+        xp, xm = x64.clone(), x64.clone()
+        xp[b, i] += h
+        xm[b, i] -= h
+        fd = (ps.gsc_loss(plan, xp, uw, s64).item() - ps.gsc_loss(plan, xm, uw, s64).item()) / (2 * h)
+        got = gl64[b, i].item()
+        assert abs(fd - got) <= 1e-5 * max(abs(fd), 1.0 / (B * K)), (b, i, fd, got)
+    _, _, gl32 = ps.gsc_loss_grad(plan, x64.float(), uw, s64.float(), want_llr_grad=True)
+    torch.cuda.synchronize()
+    ref = gl64.cpu().numpy()
+    assert np.max(np.abs(gl32.double().cpu().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
