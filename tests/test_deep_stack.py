@@ -65,6 +65,23 @@ def test_deep_pops_respect_the_iteration_bound(oracle_lib):
     assert int(stats[:, 0].max()) <= L * (nb + 9) + 2
 
 
+def test_paper_setting_noiseless_round_trip(oracle_lib):
+    """The paper's decoder setting in the oracle (systematic PC(1024,512),
+    CRC-24C, D = 8192, L = 8): noiseless frames come back as their messages
+    with status 0 and path metric 0, the search never leaving the correct path:
+    the first pop, one pop per branching node, then the complete path."""
+    N, K, crc = 1024, 512, 24
+    fr = oracle_lib.construct(N, K, 0.0)
+    msg = W.message_bits(8, 6, K - crc)
+    cw = oracle_lib.encode_batch(msg, N, K, fr, crc, systematic=True)
+    llr = W.bpsk_awgn_llr(cw, np.zeros(cw.shape, np.float32), 0.6)
+    m, pm, st, stats = oracle_lib.scs_decode_batch(llr, N, K, fr, fast=True, D=8192, L=8, crc_len=crc,
+                                                   systematic=True)
+    assert (st == 0).all() and (pm == 0).all() and np.array_equal(m, msg)
+    assert (stats[:, 0] == _nbranch(N, K, fr, True) + 2).all()
+    assert (stats[:, 1] == 0).all()  # no path switch
+
+
 # ----------------------------------------------------------------- GPU part
 def _gpu(N, K, fr, llr, fast, D, L, crc):
     torch = pytest.importorskip("torch")
