@@ -971,7 +971,8 @@ def main(argv=None) -> int:
                          "paper: the paper's decoder setting (CRC-24C, D = 8192, L = 8) over 0-3 dB")
     ap.add_argument("--serve-rate", type=float, default=0.0, help="serve workload: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="serve workload: seconds of arrivals")
-    ap.add_argument("--frames", type=int, default=0, help="frames per Eb/N0 point (default 1048576)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="frames per Eb/N0 point (default 1048576; paper workload 524288; gsc 65536)")
     ap.add_argument("--cpu-frames", type=int, default=8192, help="oracle sample per point for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=1024, help="oracle sample per point per step (reference arm)")
     ap.add_argument("--no-e2e", action="store_true")
