@@ -14,6 +14,13 @@ Prints ONE JSON line (rank 0).  Metric: decoded message bits per second
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Other workloads (--workload; each prints its own line): mixed (2,000,000
+frames of mixed codes and depths in one launch, against per-configuration
+launches), serve (Poisson arrivals, continuous batching against
+one-size-per-launch batching), gsc (genie-aided SC loss and gradient over
+per-stage scales), paper (the paper's decoder setting: systematic
+PC(1024,512), CRC-24C, D = 8192, L = 8, 524,288 frames at each of 0 ... 3 dB).
+
 Multi-GPU (torchrun, one process per GPU): every rank decodes its own
 frames (seed offset by rank) with no collective on the data path (weak
 scaling); the timed region is bracketed by barriers and the slowest rank's
