@@ -175,18 +175,26 @@ int scs_decode_batch(const polar_plan *plan, const float *d_llr, int B, int D, i
 /* scs_decode_batch without any allocation by the library (the paper has no
  * counterpart; this is a deployment variant).  For callers that cannot
  * allocate device memory at decode time -- a fixed budget reserved at
- * start-up, a real-time or callback context where cudaMalloc/cudaMallocAsync
- * may block or fail, or device memory owned by another allocator.  Same
- * arguments, outputs and results as scs_decode_batch; the caller still
- * provides every input and output buffer.
+ * start-up, a real-time loop where cudaMalloc/cudaMallocAsync may block or
+ * fail, or device memory owned by another allocator.  Same arguments, outputs
+ * and results as scs_decode_batch for D <= POLAR_MAX_D_GPU (the register
+ * stack); the memory stack of larger D needs per-call scratch and is not
+ * offered here (POLAR_ELIMIT).  The caller still provides every input and
+ * output buffer.
  *  - The scratch lives in a file-scope static device array of 16 MiB and the
- *    plan's tables are copied (asynchronously, from the plan's host memory)
- *    into a static 1 MiB device area; every GPU that loads the library holds
- *    both until the process exits.  The decoder runs as many resident warps
- *    as the 16 MiB hold, so large D and N run on fewer warps (slower, same
- *    result).  Returns POLAR_ESCRATCH when the plan's tables exceed 1 MiB or
- *    one warp's scratch, (D+1) * (ceil(N/32)+4 rounded up to 8) * 4 bytes,
- *    exceeds 16 MiB.
+ *    plan's tables are copied into a static 1 MiB device area; every GPU that
+ *    loads the library holds both until the process exits.  The decoder runs
+ *    as many resident warps as the 16 MiB hold, so large D and N run on fewer
+ *    warps (slower, same result).  Returns POLAR_ESCRATCH when the plan's
+ *    tables exceed 1 MiB or one warp's scratch, (D+1) * (ceil(N/32)+4 rounded
+ *    up to 8) * 4 bytes, exceeds 16 MiB.
+ *  - The table area remembers the plan (and the version of its tables) it
+ *    holds.  A call with another plan, or after polar_plan_set_scales changed
+ *    the plan, copies the tables from the plan's pageable host memory: CUDA
+ *    may make the host wait for earlier work on the stream before such a
+ *    copy.  A call with the plan already in the area issues no copy, only a
+ *    reset of the frame counter (a memset) and the kernel launch; it relies on the earlier
+ *    call's copy being ordered before it (the same stream, or synchronised).
  *  - No cudaMalloc, cudaMallocAsync or cudaFree is called.  The first call on
  *    a device looks up the arrays' device addresses (cudaGetSymbolAddress)
  *    with that device current; make that first call before any stream

@@ -66,6 +66,8 @@ def _load():
             lib.or_scs_decode_batch_s.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, u8p, f32p, i8p, u64p]
             lib.or_scs_decode_sx.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, C.c_int, u8p, f32p, u8p, u64p]
             lib.or_scs_decode_batch_sx.argtypes = [f32p, C.c_int, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, f32p, C.c_int, u8p, f32p, i8p, u64p]
+            lib.or_scs_decode_trace.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                                C.c_int, i32p, f32p, u8p, i32p, u8p, f32p, u8p, u64p]
             lib.or_scs_decode_exact.argtypes = [f64p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, u8p, f64p]
             lib.or_scs_decode_exact_f32.argtypes = [f32p, C.c_int, C.c_int, u8p, C.c_int, C.c_int, u8p, f32p]
             lib.or_gsc_forward.argtypes = [f64p, u8p, C.c_int, f64p, f64p]
@@ -173,6 +175,34 @@ def scs_decode(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: boo
         raise ValueError(f"or_scs_decode -> {rc}")
     stats = dict(iterations=int(st[0]), switches=int(st[1]), ops=int(st[2]), expansions=int(st[3]), max_visits=int(st[4]))
     return rc, msg, np.float32(pm.value), cw, stats
+
+
+def scs_decode_trace(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: bool, D: int, L: int,
+                     crc_len: int = 0, systematic: bool = False, max_pops: int = 4096):
+    """scs_decode with a trace of every pop (test hook).  Returns (status, msg,
+    pm, codeword, stats, trace) where trace is a list of (schedule position,
+    pm, beta array [N]) per pop, the beta array being the popped path's right
+    after its restore; a complete path has schedule position = the number of
+    schedule operations."""
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    fr = _u8(frozen)
+    msg = np.zeros(K - crc_len, np.uint8)
+    cw = np.zeros(N, np.uint8)
+    pm = C.c_float(0.0)
+    st = np.zeros(5, np.uint64)
+    sched = np.zeros(max_pops, np.int32)
+    pmt = np.zeros(max_pops, np.float32)
+    beta = np.zeros((max_pops, N), np.uint8)
+    nt = C.c_int(0)
+    rc = _load().or_scs_decode_trace(_p(llr, C.c_float), N, K, _p(fr, C.c_uint8), int(bool(fast)), D, L, crc_len,
+                                     int(bool(systematic)), max_pops, _p(sched, C.c_int), _p(pmt, C.c_float),
+                                     _p(beta, C.c_uint8), C.byref(nt), _p(msg, C.c_uint8), C.byref(pm),
+                                     _p(cw, C.c_uint8), _p(st, C.c_uint64))
+    if rc < 0:
+        raise ValueError(f"or_scs_decode_trace -> {rc}")
+    stats = dict(iterations=int(st[0]), switches=int(st[1]), ops=int(st[2]), expansions=int(st[3]), max_visits=int(st[4]))
+    trace = [(int(sched[k]), np.float32(pmt[k]), beta[k].copy()) for k in range(nt.value)]
+    return rc, msg, np.float32(pm.value), cw, stats, trace
 
 
 def scs_decode_batch(llr: np.ndarray, N: int, K: int, frozen: np.ndarray, *, fast: bool, D: int, L: int,

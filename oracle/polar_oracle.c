@@ -362,6 +362,12 @@ typedef struct {
     uint64_t st_iter, st_switch, st_ops, st_exp, st_maxcnt;
     int stack_cost;
     int systematic; /* message read from the codeword estimate (no re-encode) */
+    /* optional trace for tests: per pop, the popped path's schedule position,
+     * path metric and its beta array right after the restore */
+    int trace_max, trace_n;
+    int *trace_sched;
+    float *trace_pm;
+    uint8_t *trace_beta;
 } or_dec;
 
 static void dec_free(or_dec *d) {
@@ -691,6 +697,12 @@ static int scs_run(or_dec *d, const float *llr, uint8_t *msg_out, float *pm_out,
         int real_switch = (d->expn[j] != d->last_exp);
         /* restore the path's beta array (Sec. 4: no re-population needed) */
         memcpy(d->beta, d->bits + (size_t)j * N, (size_t)N);
+        if (d->trace_n < d->trace_max) {
+            d->trace_sched[d->trace_n] = sched;
+            d->trace_pm[d->trace_n] = pm;
+            memcpy(d->trace_beta + (size_t)d->trace_n * N, d->beta, (size_t)N);
+            d->trace_n++;
+        }
         if (real_switch) {
             d->st_switch++;
             d->st_ops += (uint64_t)words32(N);
@@ -773,6 +785,37 @@ int or_scs_decode_sx(const float *llr, int N, int K, const uint8_t *frozen, int 
     float pm = 0.0f;
     rc = scs_run(&d, llr, msg_out, &pm, cw_out);
     if (pm_out) *pm_out = pm;
+    if (stats) {
+        stats[0] = d.st_iter;
+        stats[1] = d.st_switch;
+        stats[2] = d.st_ops;
+        stats[3] = d.st_exp;
+        stats[4] = d.st_maxcnt;
+    }
+    dec_free(&d);
+    return rc;
+}
+
+/* or_scs_decode_sx with a trace of the first max_pops pops (test hook): for
+ * pop k, sched_out[k] = the popped path's schedule position (the number of
+ * schedule operations before it; nops for a complete path), pm_trace[k] its
+ * path metric and beta_trace[k * N ...] its N-entry beta array after the
+ * restore.  *n_traced = the pops recorded. */
+int or_scs_decode_trace(const float *llr, int N, int K, const uint8_t *frozen, int fast, int D, int L, int crc,
+                        int systematic, int max_pops, int *sched_out, float *pm_trace, uint8_t *beta_trace,
+                        int *n_traced, uint8_t *msg_out, float *pm_out, uint8_t *cw_out, uint64_t *stats) {
+    or_dec d;
+    int rc = dec_init(&d, N, K, frozen, fast, D, L, crc);
+    if (rc) return rc;
+    d.systematic = systematic ? 1 : 0;
+    d.trace_max = max_pops;
+    d.trace_sched = sched_out;
+    d.trace_pm = pm_trace;
+    d.trace_beta = beta_trace;
+    float pm = 0.0f;
+    rc = scs_run(&d, llr, msg_out, &pm, cw_out);
+    if (pm_out) *pm_out = pm;
+    if (n_traced) *n_traced = d.trace_n;
     if (stats) {
         stats[0] = d.st_iter;
         stats[1] = d.st_switch;

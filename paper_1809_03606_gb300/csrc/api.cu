@@ -129,6 +129,7 @@ extern "C" int polar_plan_set_scales(polar_plan *p, const float *scales) {
     } else {
         p->scales.clear();
     }
+    ++p->version;
     if (p->dev.device < 0) return 0;  // the device copy is made on first use
     int cur = -1;
     cudaGetDevice(&cur);

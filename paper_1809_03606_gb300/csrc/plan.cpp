@@ -9,6 +9,7 @@
 // 3.3 Alg. calp), and the visit-counter index of each branching node (Sec.
 // 2.2.5).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -127,6 +128,8 @@ extern "C" int polar_plan_create(int N, int K, const uint8_t *frozen, int fast_n
     if (rc) return rc;
     polar_plan *p = new (std::nothrow) polar_plan();
     if (!p) return POLAR_ENOMEM;
+    static std::atomic<uint64_t> next_serial{1};
+    p->serial = next_serial.fetch_add(1);
     try {
         p->N = N;
         p->n = 0;
@@ -302,6 +305,7 @@ extern "C" int polar_plan_set_exact(polar_plan *p, int on) {
     if (p->dev.device >= 0) return POLAR_EINVAL;  // tables already on a device
     if (on && (p->fast || !p->scales.empty())) return POLAR_EINVAL;
     p->exact = on ? 1 : 0;
+    ++p->version;
     return 0;
 }
 
@@ -312,6 +316,7 @@ extern "C" int polar_plan_set_systematic(polar_plan *p, int on) {
     try {
         if (on && !polarscs::two_pass_is_systematic(p)) return POLAR_EINVAL;
         p->systematic = on ? 1 : 0;
+        ++p->version;
         polarscs::build_crc_rows(p);
     } catch (...) {
         return POLAR_ENOMEM;

@@ -1812,17 +1812,19 @@ int read_device_ns(unsigned long long *d_out, cudaStream_t s) {
 // Decoding without any allocation by the library.
 //
 // Some callers cannot allocate device memory when they decode: code that runs
-// under a fixed memory budget reserved at start-up, callers inside a host
-// callback or a real-time loop where cudaMalloc/cudaMallocAsync may block or
-// fail, or processes whose device memory is owned by another allocator.  For
-// them scs_decode_batch_noalloc keeps the decoder's scratch (the per-warp beta
-// snapshots and the frame counter) and its copy of the plan's tables in two
-// fixed file-scope device arrays below.  Every GPU that loads the library holds
-// these arrays (16 MiB + 1 MiB) until the process exits.
+// under a fixed memory budget reserved at start-up, real-time loops where
+// cudaMalloc/cudaMallocAsync may block or fail, or processes whose device
+// memory is owned by another allocator.  For them scs_decode_batch_noalloc
+// keeps the decoder's scratch (the per-warp beta snapshots and the frame
+// counter) and its copy of the plan's tables in two fixed file-scope device
+// arrays below.  Every GPU that loads the library holds these arrays (16 MiB
+// + 1 MiB) until the process exits.
 //
 // The host needs their device addresses: in host code the names are host-side
 // stand-ins, so they are fetched once per device with cudaGetSymbolAddress,
-// with that device current, on the first call made on that device.
+// with that device current, on the first call made on that device.  The
+// table area remembers which plan (serial number and version) it holds, so a
+// call with the same plan issues no copy at all.
 // ---------------------------------------------------------------------------
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
 constexpr size_t kStaticTableBytes = size_t(1) << 20;
@@ -1835,6 +1837,7 @@ struct StaticAreas {
     bool ready = false;
     void *scratch = nullptr;
     void *tables = nullptr;
+    uint64_t serial = 0, version = 0;  // plan whose tables the area holds (0: none)
 };
 std::mutex g_static_mu;
 StaticAreas g_static_areas[64];
@@ -1857,6 +1860,13 @@ int static_areas(int dev, StaticAreas *out) {
     return 0;
 }
 
+// record which plan's tables the device's table area holds (serial 0: none)
+void static_tables_hold(int dev, uint64_t serial, uint64_t version) {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    g_static_areas[dev].serial = serial;
+    g_static_areas[dev].version = version;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
@@ -1870,8 +1880,11 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     StaticAreas areas;
     int rc = static_areas(dev, &areas);
     if (rc) return rc;
+    // the plan's tables and sizes are read under its lock (polar_plan_set_scales
+    // may replace the scales on another thread)
+    std::lock_guard<std::mutex> plan_lock(p->mu);
 
-    // the plan's tables, copied into the static table area
+    // layout of the plan's tables in the static table area
     const size_t ops_bytes = p->dev_ops.size() * sizeof(KOp);
     const size_t rows_off = align_up(ops_bytes, 256);
     const size_t rows_bytes = p->crc_rows.size() * sizeof(uint32_t);
@@ -1914,16 +1927,24 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
 
     a.counter = static_cast<unsigned *>(areas.scratch);
     a.scratch = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(areas.scratch) + 64);
-    // tables from host memory, then the frame counter back to zero (the array
-    // keeps whatever the previous call left in it)
-    e = cudaMemcpyAsync(tab, p->dev_ops.data(), ops_bytes, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && rows_bytes)
-        e = cudaMemcpyAsync(tab + rows_off, p->crc_rows.data(), rows_bytes, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && pos_bytes)
-        e = cudaMemcpyAsync(tab + pos_off, p->msg_pos.data(), pos_bytes, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && sc_bytes)
-        e = cudaMemcpyAsync(tab + sc_off, p->scales.data(), sc_bytes, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
+    // the tables, unless this plan's current version is already in the area;
+    // they come from the plan's pageable host vectors, a copy for which CUDA
+    // may first wait on the host for earlier work on the stream
+    if (areas.serial != p->serial || areas.version != p->version) {
+        static_tables_hold(dev, 0, 0);  // in flux until every copy is issued
+        e = cudaMemcpyAsync(tab, p->dev_ops.data(), ops_bytes, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess && rows_bytes)
+            e = cudaMemcpyAsync(tab + rows_off, p->crc_rows.data(), rows_bytes, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess && pos_bytes)
+            e = cudaMemcpyAsync(tab + pos_off, p->msg_pos.data(), pos_bytes, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess && sc_bytes)
+            e = cudaMemcpyAsync(tab + sc_off, p->scales.data(), sc_bytes, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        static_tables_hold(dev, p->serial, p->version);
+    }
+    // the frame counter back to zero (the array keeps whatever the previous
+    // call left in it)
+    e = cudaMemsetAsync(areas.scratch, 0, 64, stream);
     if (e != cudaSuccess) return cuda_status(e);
     e = launch_fn(fn, grid, wpb, smem, stream, a);
     return e == cudaSuccess ? 0 : cuda_status(e);

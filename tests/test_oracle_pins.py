@@ -111,6 +111,100 @@ def test_beta_memory_layout_fig_fsscsbmem(oracle_lib):
         assert st == 0 and pm == 0.0 and np.array_equal(xhat, cw) and np.array_equal(m, msg)
 
 
+def test_beta_memory_slots_fig_fsscsbmem(oracle_lib):
+    """Fig. fsscsbmem, slot by slot: the golden file names, for each step of the
+    PC(8,4) schedule, the node whose estimate the in-place beta array holds and
+    its slots.  The oracle's beta array of the path popped right after that
+    step must hold exactly the node's partial-sum estimate there (the
+    Kronecker-power encoding of the node's leaves, Sec. 2.2.1), and, after the
+    REP node, the SPC slots must still be untouched (zero)."""
+    rows = read_golden("pc8_4_beta_memory.txt")
+    sched = [(op, int(l), int(p)) for op, l, p in read_golden("pc8_4_fssc_schedule.txt")]
+    after = {"after_REP": sched.index(("REP", 2, 0)) + 1, "after_SPC": sched.index(("SPC", 2, 1)) + 1,
+             "after_beta": len(sched)}
+    fr = oracle_lib.construct(8, 4, 0.0)
+    rng = np.random.default_rng(4)
+    for _ in range(24):
+        msg = rng.integers(0, 2, 4).astype(np.uint8)
+        cw = oracle_lib.encode_msg(msg, 8, 4, fr)
+        u = np.zeros(8, np.uint8)
+        u[fr == 0] = msg
+        llr = np.where(cw == 1, -8.0, 8.0).astype(np.float32)
+        st, m, pm, xhat, stats, trace = oracle_lib.scs_decode_trace(llr, 8, 4, fr, fast=True, D=1, L=4)
+        assert st == 0 and np.array_equal(m, msg)
+        popped = {t: beta for t, _, beta in trace}
+        for step, lam, phi, first, last in rows:
+            lam, phi, first, last = int(lam), int(phi), int(first), int(last)
+            Lam = 1 << lam
+            assert (first, last) == (phi * Lam, (phi + 1) * Lam - 1)  # the slots of node (lambda, phi)
+            beta = popped[after[step]]
+            assert np.array_equal(beta[first:last + 1], tb.encode_matrix(u[first:last + 1])), (step, msg)
+            if step == "after_REP":
+                assert not np.any(beta[last + 1:])
+        assert np.array_equal(popped[after["after_beta"]], cw)
+
+
+def _hand_cases():
+    cases, cur = [], None
+    for row in read_golden("op_counts_hand.txt"):
+        key, vals = row[0], row[1:]
+        if key == "case":
+            cur = dict(name=vals[0], steps=[])
+            cases.append(cur)
+        elif key == "step":
+            cur["steps"].append(int(vals[0]))
+        elif key in ("code", "frozen", "stack", "total", "codeword"):
+            cur[key] = [int(v) for v in vals]
+        elif key == "llr":
+            cur[key] = np.array([float(v) for v in vals], np.float32)
+    return cases
+
+
+@pytest.mark.parametrize("case", _hand_cases(), ids=lambda c: c["name"])
+def test_operation_counts_derived_by_hand(oracle_lib, case):
+    """The operation counters (the numerator of the roofline fraction) against
+    counts worked out by hand from the counting convention for the worked
+    example of Fig. fsscsch and two small bit-level codes, with and without a
+    path switch (one of them with an alpha recompute below the root)."""
+    N, K, fast = case["code"]
+    D, L = case["stack"]
+    ops, pops, switches, exps, pm_want = case["total"]
+    assert sum(case["steps"]) == ops  # the file's own arithmetic
+    fr = np.array(case["frozen"], np.uint8)
+    st, m, pm, xhat, stats = oracle_lib.scs_decode(case["llr"], N, K, fr, fast=bool(fast), D=D, L=L)
+    assert st == 0
+    assert (stats["ops"], stats["iterations"], stats["switches"], stats["expansions"]) == (ops, pops, switches, exps)
+    assert float(pm) == float(pm_want)
+    assert np.array_equal(xhat, np.array(case["codeword"], np.uint8))
+    assert tb.discrepancy(case["llr"], xhat) == float(pm)  # and the metric is the codeword's discrepancy
+
+
+def test_crc_failure_returns_first_complete_path(oracle_lib):
+    """Sec. 2.2.5 with reading R12: after L complete paths have failed the CRC,
+    the decoder returns the FIRST complete path popped (status CRC_FAIL), not
+    the last or the best one.  Frames are chosen where two different complete
+    paths were popped and both fail the CRC (checked by long division)."""
+    N, K, crc, D, L = 64, 32, 8, 32, 2
+    fr, msg, cw, llr = _frames(oracle_lib, N, K, crc, 400, 0.0, seed=51)
+    nops = len(oracle_lib.schedule(N, fr, True))
+    checked = 0
+    for b in range(llr.shape[0]):
+        st, m, pm, xhat, stats, trace = oracle_lib.scs_decode_trace(llr[b], N, K, fr, fast=True, D=D, L=L,
+                                                                    crc_len=crc)
+        done = [(p, beta) for t, p, beta in trace if t == nops]
+        if st != 1 or len(done) != L or np.array_equal(done[0][1], done[1][1]):
+            continue
+        for p, beta in done:  # both complete paths fail the CRC
+            u = tb.encode_matrix(beta)[fr == 0]
+            want = tb.crc_longdiv(u[:K - crc], crc, 0x07)
+            got = int("".join(str(int(v)) for v in u[K - crc:]), 2)
+            assert got != want
+        assert np.array_equal(xhat, done[0][1]) and pm == done[0][0]
+        assert not np.array_equal(xhat, done[1][1])
+        checked += 1
+    assert checked >= 5
+
+
 # ----------------------------------------------------------------------- CRC
 def test_crc_catalogue_check_values(oracle_lib):
     bits = np.unpackbits(np.frombuffer(b"123456789", np.uint8))

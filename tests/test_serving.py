@@ -1,7 +1,9 @@
 """Serving with continuous batching (polar_serve) and its one-size-per-launch
-baseline: every request's result is the same as decoding it alone, under
-arena pressure (admission stalls) and interleaving; a device wait that runs
-out ends the engine cleanly with POLAR_ETIMEOUT."""
+baseline: every served request's result equals the CPU oracle's decode of
+its frame (message bits, path-metric bits, status) and the same frame
+decoded alone on the GPU, under arena pressure (admission stalls) and
+interleaving; a device wait that runs out ends the engine cleanly with
+POLAR_ETIMEOUT."""
 import numpy as np
 import pytest
 
@@ -36,6 +38,19 @@ def pool(oracle_lib):
     return dict(plans=plans, pset=ps.PlanSet(plans), idx=idx, D=D, rows=rows, off=off, flat=flat, P=P)
 
 
+def _oracle(pool, oracle_lib):
+    """The CPU oracle's (message bits, pm, status) of every pool frame, decoded
+    with its own code, D and L = D (fast nodes, CRC-8)."""
+    out = {}
+    for p in range(pool["P"]):
+        N, K, crc = CODES[pool["idx"][p]]
+        d = int(pool["D"][p])
+        st, m, pm, _, _ = oracle_lib.scs_decode(pool["rows"][p], N, K, pool["plans"][pool["idx"][p]].frozen,
+                                                fast=True, D=d, L=d, crc_len=crc)
+        out[p] = (m, np.float32(pm), int(st))
+    return out
+
+
 def _solo(pool):
     """pm, status and message words of every pool frame decoded alone."""
     out = {}
@@ -57,8 +72,16 @@ def _requests(pool, R, rate, seed):
     return req, arr, p
 
 
-def test_served_results_equal_solo_under_arena_pressure(pool):
+def test_served_results_equal_oracle_and_solo_under_arena_pressure(pool, oracle_lib):
     solo = _solo(pool)
+    ref = _oracle(pool, oracle_lib)
+    # the GPU's solo decode is itself bit-exact against the oracle on the pool
+    for p in range(pool["P"]):
+        m_o, pm_o, st_o = ref[p]
+        pm_s, st_s, info_s = solo[p]
+        kmsg = m_o.size
+        assert np.array_equal(ps.unpack_bits(info_s[None, :], kmsg)[0], m_o), p
+        assert np.float32(pm_s).view(np.uint32) == pm_o.view(np.uint32) and st_s == st_o, p
     R = 3000
     req, arr, p = _requests(pool, R, 3e5, seed=21)
     words = np.array([pool["plans"][i].msg_words for i in req[:, 0]], np.int64)
@@ -70,8 +93,15 @@ def test_served_results_equal_solo_under_arena_pressure(pool):
     assert np.all(out["latency"] >= 0)
     for r in range(R):
         pm_s, st_s, info_s = solo[int(p[r])]
+        m_o, pm_o, st_o = ref[int(p[r])]
+        served = out["info"][ioff[r]:ioff[r] + words[r]]
+        # against the oracle: message bits, path-metric bits, status
+        assert np.array_equal(ps.unpack_bits(np.asarray(served)[None, :], m_o.size)[0], m_o), r
+        assert np.float32(out["pm"][r]).view(np.uint32) == pm_o.view(np.uint32), r
+        assert int(out["status"][r]) == st_o, r
+        # and against the same frame decoded alone
         assert np.float32(out["pm"][r]) == np.float32(pm_s) and out["status"][r] == st_s
-        assert np.array_equal(out["info"][ioff[r]:ioff[r] + words[r]], info_s)
+        assert np.array_equal(served, info_s)
     base = ps.polar_serve_baseline(pool["pset"], req, arr, pool["flat"], pool["off"], arena_floats=200000,
                                    interval_s=2e-3, wait_s=20.0)
     assert base["rc"] == 0 and base["report"]["completed"] == R

@@ -1,10 +1,10 @@
 """The allocation-free decode entry point against the regular one.
 
 scs_decode_batch_noalloc serves callers that cannot allocate device memory
-when they decode (a budget fixed at start-up, a real-time or callback
-context, memory owned by another allocator): its scratch is a fixed static
-device array inside the library instead of a per-call stream-ordered
-allocation.  Its results must be exactly those of scs_decode_batch.  Two
+when they decode (a budget fixed at start-up, a real-time loop where an
+allocation may block or fail, memory owned by another allocator): its
+scratch is a fixed static device array inside the library instead of a
+per-call stream-ordered allocation.  Its results must be exactly those of scs_decode_batch.  Two
 calls in a row, with different codes, check that the shared static memory
 (tables, frame counter, snapshots) left over from one call does not leak
 into the next.  This file is collected last so that a failure here comes
@@ -100,3 +100,48 @@ def test_noalloc_plan_modes(oracle_lib):
         for r, q in zip(ref, got):
             assert torch.equal(r, q), m
         assert int((ref[2] == 0).sum()) > 0
+
+
+def test_noalloc_when_the_static_scratch_limits_residency(oracle_lib):
+    """PC(2048,1024) CRC-8 with D = 64: one warp's snapshots take 18,720 bytes,
+    so the 16 MiB array holds 896 warps, fewer than the persistent grid would
+    otherwise start; the reduced grid must give exactly the regular outputs."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ps.load(build_if_missing=True)
+    N, K, crc, D, L, B = 2048, 1024, 8, 64, 64, 6000
+    fr, llr = _frames(oracle_lib, N, K, crc, B, 2.0, seed=43)
+    plan = ps.Plan(N, K, fr, fast_nodes=True, crc=crc)
+    x = torch.from_numpy(llr).cuda()
+    got, ref = _outputs(plan, B), _outputs(plan, B)
+    ps.scs_decode_batch_noalloc(plan, x, D, L, *got)
+    ps.scs_decode_batch(plan, x, D, L, *ref)
+    torch.cuda.synchronize()
+    for r, q in zip(ref, got):
+        assert torch.equal(r, q)
+    assert int((ref[2] == 0).sum()) > 0
+
+
+def test_noalloc_table_area_follows_plan_changes(oracle_lib):
+    """The static table area keeps the last plan's tables: alternating plans,
+    repeating one, and changing a plan's stage scales between calls must each
+    decode with the right tables."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ps.load(build_if_missing=True)
+    fr_a, llr_a = _frames(oracle_lib, 512, 256, 8, 800, 2.0, seed=44)
+    fr_b, llr_b = _frames(oracle_lib, 256, 128, 0, 800, 2.5, seed=45)
+    pa = ps.Plan(512, 256, fr_a, fast_nodes=True, crc=8)
+    pb = ps.Plan(256, 128, fr_b, fast_nodes=True, crc=0)
+    xa, xb = torch.from_numpy(llr_a).cuda(), torch.from_numpy(llr_b).cuda()
+    scales = np.linspace(0.7, 1.1, 9).astype(np.float32)
+    for plan, x, sc in ((pa, xa, None), (pb, xb, None), (pa, xa, None), (pa, xa, None), (pa, xa, scales),
+                        (pa, xa, scales), (pa, xa, None)):
+        plan.set_scales(sc)
+        got, ref = _outputs(plan, 800), _outputs(plan, 800)
+        ps.scs_decode_batch_noalloc(plan, x, 16, 16, *got)
+        torch.cuda.synchronize()
+        ps.scs_decode_batch(plan, x, 16, 16, *ref)
+        torch.cuda.synchronize()
+        for r, q in zip(ref, got):
+            assert torch.equal(r, q), (plan.N, sc is None)
