@@ -126,15 +126,6 @@ int polar_plan_set_systematic(polar_plan *plan, int on);
  * device). */
 int polar_plan_set_exact(polar_plan *plan, int on);
 
-/* How many lanes of a warp decode one frame in scs_decode_batch and
- * scs_decode_batch_noalloc (a GPU mapping, not a construct of the paper; the
- * decoded results do not depend on it): 8, 16 or 32 (a warp decodes 32 /
- * lanes frames at once, each with its own stack of Sec. 2.2.5 spread over its
- * lanes), or 0 = automatic (the default: the measured fastest mapping for
- * the plan and D).  Exact-f plans and the memory stack (D > 64) always use
- * 32.  Host only.  Errors: POLAR_EINVAL (NULL plan, another value). */
-int polar_plan_set_lanes(polar_plan *plan, int lanes);
-
 /* Release a plan and its device copy (synchronous; no call using it may be
  * in flight).  NULL is ignored. */
 void polar_plan_destroy(polar_plan *plan);

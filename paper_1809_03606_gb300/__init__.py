@@ -30,7 +30,6 @@ EXPORTED = (
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
     "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64", "polar_plan_set_scales", "polar_mixed_order",
     "polar_serve", "polar_serve_baseline", "polar_plan_set_systematic", "polar_plan_set_exact",
-    "polar_plan_set_lanes",
 )
 
 _lock = threading.Lock()
@@ -70,7 +69,6 @@ def load(build_if_missing: bool = False):
         lib.polar_plan_set_scales.argtypes = [vp, vp]
         lib.polar_plan_set_systematic.argtypes = [vp, i32]
         lib.polar_plan_set_exact.argtypes = [vp, i32]
-        lib.polar_plan_set_lanes.argtypes = [vp, i32]
         lib.polar_encode_batch.argtypes = [vp, vp, i32, vp, vp]
         lib.polar_encode.argtypes = [vp, i32, i32, vp, i32, vp]
         lib.scs_decode_batch.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
@@ -159,10 +157,6 @@ class Plan:
 
     def schedule(self) -> list[tuple[str, int, int]]:
         return polar_plan_schedule(self)
-
-    def set_lanes(self, lanes: int) -> None:
-        """Lanes of a warp per decoded frame (8, 16, 32; 0 = automatic)."""
-        _check("polar_plan_set_lanes", load().polar_plan_set_lanes(self.handle, int(lanes)))
 
     def set_scales(self, scales) -> None:
         """Per-stage min-sum scales for decoding (None: plain min-sum)."""

@@ -324,13 +324,6 @@ extern "C" int polar_plan_set_systematic(polar_plan *p, int on) {
     return 0;
 }
 
-extern "C" int polar_plan_set_lanes(polar_plan *p, int lanes) {
-    if (!p || (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32)) return POLAR_EINVAL;
-    std::lock_guard<std::mutex> g(p->mu);
-    p->lanes = lanes;
-    return 0;
-}
-
 extern "C" int polar_plan_schedule(const polar_plan *p, int32_t *ops_out, int max_ops) {
     if (!p || (max_ops > 0 && !ops_out)) return POLAR_EINVAL;
     const int nops = int(p->ops.size());

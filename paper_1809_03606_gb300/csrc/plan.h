@@ -71,7 +71,6 @@ struct polar_plan {
     std::vector<uint32_t> info_bits;  // W words: 1 = information position
     int systematic = 0;               // codeword carries the information bits
     int exact = 0;                    // exact-f decoding (box-plus f, exact leaf metric)
-    int lanes = 0;                    // lanes per frame of uniform launches (0: automatic)
     // identity of the plan's tables: a process-wide serial number given at
     // creation and a version bumped (under mu) by every call that changes
     // them; lets a copy of the tables on a device be recognised as current

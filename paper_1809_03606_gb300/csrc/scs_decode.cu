@@ -91,9 +91,9 @@ struct Args {
     int8_t *status_out;
     uint32_t *stats_out;
     uint32_t *scratch;
-    long long scratch_stride;   // scratch words per frame group
+    long long scratch_stride;   // snapshot words per warp
     unsigned *counter;
-    int warp_smem;              // bytes of shared memory per frame (per warp: 32 / G of them)
+    int warp_smem;              // bytes of shared memory per warp
     int llr_vec;                // the LLR buffer is 16-byte aligned
     int chunk;                  // frames claimed per atomic
     // served mode: requests become decodable when the host publishes them
@@ -163,84 +163,57 @@ __device__ __forceinline__ float pen_transform(float x, int mode) {
     return (mode == 1) == neg ? fabsf(x) : 0.0f;
 }
 
-// ---- lane groups ----
-// A frame is decoded by a group of G consecutive lanes of a warp (G = 8, 16
-// or 32), so a warp decodes 32 / G frames at once.  Every reduction,
-// shuffle, ballot and barrier of a frame names only its group's lanes; when
-// the groups of a warp sit at the same step they share its instructions.
-template <int G>
-struct Grp {
-    static constexpr uint32_t GM = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
-    int lane;       // lane within the group
-    int gbase;      // first lane of the group in the warp
-    unsigned mask;  // the group's lanes
-    __device__ __forceinline__ uint32_t ballot(bool p) const { return (__ballot_sync(mask, p) >> gbase) & GM; }
-    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
-    __device__ __forceinline__ uint32_t shfl(uint32_t v, int src) const { return __shfl_sync(mask, v, src, G); }
-    __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(mask, v, src, G); }
-    __device__ __forceinline__ float shfl(float v, int src) const { return __shfl_sync(mask, v, src, G); }
-    __device__ __forceinline__ float shfl_down(float v, int d) const { return __shfl_down_sync(mask, v, d, G); }
-    __device__ __forceinline__ uint32_t rmin(uint32_t v) const { return __reduce_min_sync(mask, v); }
-    __device__ __forceinline__ uint32_t rmax(uint32_t v) const { return __reduce_max_sync(mask, v); }
-    __device__ __forceinline__ uint32_t ror(uint32_t v) const { return __reduce_or_sync(mask, v); }
-    __device__ __forceinline__ uint32_t rxor(uint32_t v) const { return __reduce_xor_sync(mask, v); }
-};
-
-// Node reductions over more than 4G values (the few wide Rate-0, REP, Rate-1
-// and SPC nodes): out of line, so that the per-op code the warps share stays
-// small.
+// Node reductions over more than 32 values (the few Rate-0, REP, Rate-1 and
+// SPC nodes above stage 5): out of line, so that the per-op code the warps
+// share stays small.
 
 // sum of the node's values (transformed by `mode`) in halving order; levels
-// wider than the group are written into the free alpha stages below the node
-template <int G>
-__device__ __noinline__ float node_sum_wide(float *alpha, const float *A, int len, int mode, Grp<G> g) {
-    const int lane = g.lane;
+// wider than a warp are written into the free alpha stages below the node
+__device__ __noinline__ float node_sum_wide(float *alpha, const float *A, int len, int mode, int lane) {
     int h = len >> 1;
     float *dst = alpha + h;
     #pragma unroll 1
-    for (int i = lane; i < h; i += G) dst[i] = __fadd_rn(pen_transform(A[i], mode), pen_transform(A[i + h], mode));
-    g.sync();
+    for (int i = lane; i < h; i += 32) dst[i] = __fadd_rn(pen_transform(A[i], mode), pen_transform(A[i + h], mode));
+    __syncwarp();
     const float *src = dst;
-    while (h > G) {
+    while (h > 32) {
         h >>= 1;
         float *d2 = alpha + h;
         #pragma unroll 1
-        for (int i = lane; i < h; i += G) d2[i] = __fadd_rn(src[i], src[i + h]);
-        g.sync();
+        for (int i = lane; i < h; i += 32) d2[i] = __fadd_rn(src[i], src[i + h]);
+        __syncwarp();
         src = d2;
     }
     float v = src[lane];
-    g.sync();
-    for (int k = G / 2; k >= 1; k >>= 1) {
-        const float o = g.shfl_down(v, k);
+    __syncwarp();
+    for (int k = 16; k >= 1; k >>= 1) {
+        const float o = __shfl_down_sync(FULL, v, k);
         if (lane < k) v = __fadd_rn(v, o);
     }
-    return g.shfl(v, 0);
+    return __shfl_sync(FULL, v, 0);
 }
 
 // path switch: the popped path's beta from its snapshot (the node's hard
 // decisions) with its flips applied; returns the first bit position where
 // it may differ from the beta it replaces (out of line)
-template <int G>
-__device__ __noinline__ int restore_switch(const uint32_t *sp, uint32_t *beta, int W, uint32_t mask, Grp<G> g) {
-    const int lane = g.lane;
+__device__ __noinline__ int restore_switch(const uint32_t *sp, uint32_t *beta, int W, uint32_t mask, int lane) {
     const uint32_t m01 = sp[W], m23 = sp[W + 1];
     const int ss = int(sp[W + 2]), slam = int(sp[W + 3]);
     uint32_t dl = EMPTY;
     #pragma unroll 1
-    for (int k = lane; k < W; k += G) {
+    for (int k = lane; k < W; k += 32) {
         const uint32_t nv = sp[k];
         const uint32_t x = nv ^ beta[k];
         beta[k] = nv;
         if (x && dl == EMPTY) dl = uint32_t(32 * k + __ffs(x) - 1);
     }
-    dl = g.rmin(dl);
-    g.sync();
+    dl = __reduce_min_sync(FULL, dl);
+    __syncwarp();
     if (mask & FLIP_ALL) {
         const int len = 1 << slam;
         if (len >= 32) {
             #pragma unroll 1
-            for (int k = lane; k < (len >> 5); k += G) beta[(ss >> 5) + k] ^= FULL;
+            for (int k = lane; k < (len >> 5); k += 32) beta[(ss >> 5) + k] ^= FULL;
         } else if (lane == 0) {
             beta[ss >> 5] ^= ((1u << len) - 1u) << (ss & 31);
         }
@@ -254,20 +227,19 @@ __device__ __noinline__ int restore_switch(const uint32_t *sp, uint32_t *beta, i
                 beta[pos >> 5] ^= 1u << (pos & 31);
             }
     }
-    g.sync();
+    __syncwarp();
     return int(min(dl, uint32_t(ss)));  // the flips only touch [ss, ...)
 }
 
 // f and g from the channel LLRs (the root stage, in global memory), out of
 // line: vector loads when the rows are 16-byte aligned
-template <int G>
 __device__ __noinline__ void f_root(const float *P, float *C, int len, float sv, int vec, int exact, int lane) {
     if (exact) {
         #pragma unroll 1
-        for (int i = lane; i < len; i += G) C[i] = f_exact(P[i], P[i + len]);
-    } else if (vec && len >= 4 * G) {
+        for (int i = lane; i < len; i += 32) C[i] = f_exact(P[i], P[i + len]);
+    } else if (vec && len >= 128) {
         #pragma unroll 1
-        for (int i = 4 * lane; i < len; i += 4 * G) {
+        for (int i = 4 * lane; i < len; i += 128) {
             const float4 x = *reinterpret_cast<const float4 *>(P + i);
             const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
             float4 r;
@@ -279,16 +251,15 @@ __device__ __noinline__ void f_root(const float *P, float *C, int len, float sv,
         }
     } else {
         #pragma unroll 1
-        for (int i = lane; i < len; i += G) C[i] = __fmul_rn(sv, f_minsum(P[i], P[i + len]));
+        for (int i = lane; i < len; i += 32) C[i] = __fmul_rn(sv, f_minsum(P[i], P[i + len]));
     }
 }
 
-template <int G>
 __device__ __noinline__ void g_root(const float *P, float *C, const uint32_t *beta, int len, int sl, int vec,
                                     int lane) {
-    if (vec && len >= 4 * G) {
+    if (vec && len >= 128) {
         #pragma unroll 1
-        for (int i = 4 * lane; i < len; i += 4 * G) {
+        for (int i = 4 * lane; i < len; i += 128) {
             const int pos = sl + i;
             const uint32_t bits = beta[pos >> 5] >> (pos & 31);
             const float4 x = *reinterpret_cast<const float4 *>(P + i);
@@ -302,7 +273,7 @@ __device__ __noinline__ void g_root(const float *P, float *C, const uint32_t *be
         }
     } else {
         #pragma unroll 1
-        for (int i = lane; i < len; i += G) {
+        for (int i = lane; i < len; i += 32) {
             const int pos = sl + i;
             const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
             C[i] = g_op(P[i], P[i + len], bit);
@@ -315,17 +286,15 @@ struct Least {
     float mag[4];
 };
 
-// the k least reliable of `len` > 4G values (|alpha|, ties to the lower index)
-template <int G>
-__device__ __noinline__ Least node_least_wide(const float *A, int len, int k, Grp<G> g) {
-    const int lane = g.lane;
+// the k least reliable of `len` > 32 values (|alpha|, ties to the lower index)
+__device__ __noinline__ Least node_least_wide(const float *A, int len, int k, int lane) {
     Least r{{0, 0, 0, 0}, {0.0f, 0.0f, 0.0f, 0.0f}};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j >= k) break;
         uint32_t bv = EMPTY, bi = EMPTY;
         #pragma unroll 1
-        for (int i = lane; i < len; i += G) {
+        for (int i = lane; i < len; i += 32) {
             bool used = false;
 #pragma unroll
             for (int q = 0; q < 4; ++q) used |= (q < j) && (r.m[q] == i);
@@ -336,25 +305,22 @@ __device__ __noinline__ Least node_least_wide(const float *A, int len, int k, Gr
                 bi = uint32_t(i);
             }
         }
-        const uint32_t gv = g.rmin(bv);
-        const uint32_t gi = g.rmin(bv == gv ? bi : EMPTY);
+        const uint32_t gv = __reduce_min_sync(FULL, bv);
+        const uint32_t gi = __reduce_min_sync(FULL, bv == gv ? bi : EMPTY);
         r.m[j] = int(gi);
         r.mag[j] = __uint_as_float(gv);
     }
     return r;
 }
 
-// The frame a group decodes: its shared-memory alpha tree, beta array and
-// visit counters, its scratch, and its channel LLRs.
-template <int G>
-struct Frame {
-    Grp<G> g;
+struct Warp {
+    const int lane;
     const int n;          // stage of the root
     const int llr_vec;    // the root may be read with vector loads
     float *alpha;     // shared: stage lambda at alpha + 2^lambda
     uint32_t *beta;   // shared: W words
     uint8_t *cnt;     // shared: visit counters
-    uint32_t *scr;    // global: snapshot slots
+    uint32_t *scr;    // global: (D + 1) snapshot slots
     const float *root;
     const float *scales;  // f output scale per stage, or null (plain min-sum)
 
@@ -365,22 +331,21 @@ struct Frame {
     // identity, for plain min-sum); EXACT: the box-plus f itself
     template <bool EXACT>
     __device__ void op_f(int lamc) const {
-        const int lane = g.lane;
         const int len = 1 << lamc;
         float *C = alpha + len;
         const float sv = scales ? __ldg(scales + lamc) : 1.0f;
         if (lamc + 1 == n) {
-            f_root<G>(root, C, len, sv, llr_vec, EXACT ? 1 : 0, lane);
-            g.sync();
+            f_root(root, C, len, sv, llr_vec, EXACT ? 1 : 0, lane);
+            __syncwarp();
             return;
         }
         const float *P = alpha + 2 * len;
         if (EXACT) {
             #pragma unroll 1
-            for (int i = lane; i < len; i += G) C[i] = f_exact(P[i], P[i + len]);
-        } else if (len >= 4 * G) {
+            for (int i = lane; i < len; i += 32) C[i] = f_exact(P[i], P[i + len]);
+        } else if (len >= 128) {
             #pragma unroll 1
-            for (int i = 4 * lane; i < len; i += 4 * G) {
+            for (int i = 4 * lane; i < len; i += 128) {
                 const float4 x = *reinterpret_cast<const float4 *>(P + i);
                 const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
                 float4 r;
@@ -392,27 +357,26 @@ struct Frame {
             }
         } else {
             #pragma unroll 1
-            for (int i = lane; i < len; i += G) C[i] = __fmul_rn(sv, f_minsum(P[i], P[i + len]));
+            for (int i = lane; i < len; i += 32) C[i] = __fmul_rn(sv, f_minsum(P[i], P[i + len]));
         }
-        g.sync();
+        __syncwarp();
     }
 
     // alpha of the odd child (lamc, sc) from its parent and the left
     // sibling's bits beta[sc - 2^lamc, sc) (Eq. llrcalc, g)
     __device__ void op_g(int lamc, int sc) const {
-        const int lane = g.lane;
         const int len = 1 << lamc;
         const int sl = sc - len;
         float *C = alpha + len;
         if (lamc + 1 == n) {
-            g_root<G>(root, C, beta, len, sl, llr_vec, lane);
-            g.sync();
+            g_root(root, C, beta, len, sl, llr_vec, lane);
+            __syncwarp();
             return;
         }
         const float *P = alpha + 2 * len;
-        if (len >= 4 * G) {
+        if (len >= 128) {
             #pragma unroll 1
-            for (int i = 4 * lane; i < len; i += 4 * G) {
+            for (int i = 4 * lane; i < len; i += 128) {
                 const int pos = sl + i;  // a multiple of 4: the 4 bits share a word
                 const uint32_t bits = beta[pos >> 5] >> (pos & 31);
                 const float4 x = *reinterpret_cast<const float4 *>(P + i);
@@ -426,202 +390,116 @@ struct Frame {
             }
         } else {
             #pragma unroll 1
-            for (int i = lane; i < len; i += G) {
+            for (int i = lane; i < len; i += 32) {
                 const int pos = sl + i;
                 const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
                 C[i] = g_op(P[i], P[i + len], bit);
             }
         }
-        g.sync();
-    }
-
-    // lock-step form of op_f and op_g (min-sum): the alpha of child (lamc, sc),
-    // the G rule if `isg`, else the (scaled) F rule, in one code path for
-    // both -- each element computes f and g and keeps one -- so that the
-    // groups of a warp at different alpha ops share the instructions
-    __device__ void op_fg(int lamc, int sc, bool isg) const {
-        const int lane = g.lane;
-        const int len = 1 << lamc;
-        const int sl = sc - len;
-        float *C = alpha + len;
-        const bool top = lamc + 1 == n;
-        const float *P = top ? root : alpha + 2 * len;
-        const float sv = (!isg && scales) ? __ldg(scales + lamc) : 1.0f;
-        const bool vec = (!top || llr_vec) && len >= 4 * G;
-        #pragma unroll 1
-        for (int i = 4 * lane; vec && i < len; i += 4 * G) {
-            const int pos = isg ? sl + i : 0;  // a multiple of 4: the 4 bits share a word
-            const uint32_t bits = beta[pos >> 5] >> (pos & 31);
-            const float4 x = *reinterpret_cast<const float4 *>(P + i);
-            const float4 y = *reinterpret_cast<const float4 *>(P + i + len);
-            float4 r;
-            r.x = isg ? g_op(x.x, y.x, bits & 1u) : __fmul_rn(sv, f_minsum(x.x, y.x));
-            r.y = isg ? g_op(x.y, y.y, (bits >> 1) & 1u) : __fmul_rn(sv, f_minsum(x.y, y.y));
-            r.z = isg ? g_op(x.z, y.z, (bits >> 2) & 1u) : __fmul_rn(sv, f_minsum(x.z, y.z));
-            r.w = isg ? g_op(x.w, y.w, (bits >> 3) & 1u) : __fmul_rn(sv, f_minsum(x.w, y.w));
-            *reinterpret_cast<float4 *>(C + i) = r;
-        }
-        #pragma unroll 1
-        for (int i = lane; !vec && i < len; i += G) {
-            const int pos = isg ? sl + i : 0;
-            const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
-            const float a = P[i], b = P[i + len];
-            C[i] = isg ? g_op(a, b, bit) : __fmul_rn(sv, f_minsum(a, b));
-        }
-        g.sync();
+        __syncwarp();
     }
 
     // in-place beta operation of Sec. 4: beta[sl + i] ^= beta[sr + i]
     __device__ void op_comb(int lamc, int sr) const {
-        const int lane = g.lane;
         const int len = 1 << lamc;
         const int sl = sr - len;
         if (len >= 32) {
             const int wl = sl >> 5, wr = sr >> 5, nw = len >> 5;
             #pragma unroll 1
-            for (int k = lane; k < nw; k += G) beta[wl + k] ^= beta[wr + k];
+            for (int k = lane; k < nw; k += 32) beta[wl + k] ^= beta[wr + k];
         } else if (lane == 0) {
             const int w = sl >> 5, off = sl & 31;
             const uint32_t v = beta[w];
             const uint32_t mask = ((1u << len) - 1u) << off;
             beta[w] = v ^ ((v >> len) & mask);
         }
-        g.sync();
+        __syncwarp();
     }
 
     // set beta[s, s + 2^lam) to all-zero or all-one
     __device__ void set_range(int lam, int s, uint32_t bit) const {
-        const int lane = g.lane;
         const int len = 1 << lam;
         if (len >= 32) {
             const uint32_t v = bit ? FULL : 0u;
             #pragma unroll 1
-            for (int k = lane; k < (len >> 5); k += G) beta[(s >> 5) + k] = v;
+            for (int k = lane; k < (len >> 5); k += 32) beta[(s >> 5) + k] = v;
         } else if (lane == 0) {
             const uint32_t mask = ((1u << len) - 1u) << (s & 31);
             const uint32_t w = beta[s >> 5];
             beta[s >> 5] = bit ? (w | mask) : (w & ~mask);
         }
-        g.sync();
+        __syncwarp();
     }
 
     // ---- reductions of the node decoders over the node's alpha ----
     // hard decisions into beta[s, s + 2^lam); returns their parity (XOR)
     __device__ uint32_t node_hd(int lam, int s) const {
-        const int lane = g.lane;
         const int len = 1 << lam;
         const float *A = stage(lam);
         uint32_t par = 0;
         if (len >= 32) {
             for (int c = 0; c < (len >> 5); ++c) {
-                uint32_t bits = 0u;
-#pragma unroll
-                for (int sub = 0; sub < 32 / G; ++sub) bits |= g.ballot(A[c * 32 + sub * G + lane] < 0.0f) << (sub * G);
+                const uint32_t bits = __ballot_sync(FULL, A[c * 32 + lane] < 0.0f);
                 par ^= __popc(bits) & 1u;
                 if (lane == 0) beta[(s >> 5) + c] = bits;
             }
         } else {
-            uint32_t bits = 0u;
-#pragma unroll
-            for (int sub = 0; sub < 32 / G; ++sub) {
-                if (sub * G >= len) break;
-                const int i = sub * G + lane;
-                bits |= g.ballot(i < len && A[i] < 0.0f) << (sub * G);
-            }
+            const uint32_t bits = __ballot_sync(FULL, lane < len && A[lane] < 0.0f);
             par = __popc(bits) & 1u;
             if (lane == 0) {
                 const uint32_t mask = ((1u << len) - 1u) << (s & 31);
                 beta[s >> 5] = (beta[s >> 5] & ~mask) | (bits << (s & 31));
             }
         }
-        g.sync();
+        __syncwarp();
         return par;
     }
 
     // sum over the node's 2^lam alpha values (transformed) in halving order:
-    // v[i] += v[i + h], h = 2^(lam-1) ... 1.  A lane holds the values
-    // lane + jG; the levels h >= G add values of one lane, in registers up to
-    // 4 values a lane, in the free alpha stages below the node beyond.
+    // v[i] += v[i + h], h = 2^(lam-1) ... 1.  Levels wider than a warp are
+    // written into the free alpha stages below the node.
     __device__ float node_sum(int lam, int mode) const {
-        const int lane = g.lane;
         const int len = 1 << lam;
         const float *A = stage(lam);
-        if (len > 4 * G) return node_sum_wide<G>(alpha, A, len, mode, g);
-        float v;
-        if (len <= G) {
-            v = lane < len ? pen_transform(A[lane], mode) : 0.0f;
-        } else {
-            v = pen_transform(A[lane], mode);
-            float v1 = pen_transform(A[lane + G], mode);
-            if (len == 4 * G) {
-                v = __fadd_rn(v, pen_transform(A[lane + 2 * G], mode));
-                v1 = __fadd_rn(v1, pen_transform(A[lane + 3 * G], mode));
+        if (len <= 32) {
+            float v = lane < len ? pen_transform(A[lane], mode) : 0.0f;
+            for (int h = len >> 1; h >= 1; h >>= 1) {
+                const float o = __shfl_down_sync(FULL, v, h);
+                if (lane < h) v = __fadd_rn(v, o);
             }
-            v = __fadd_rn(v, v1);
+            return __shfl_sync(FULL, v, 0);
         }
-        for (int h = min(len, G) >> 1; h >= 1; h >>= 1) {
-            const float o = g.shfl_down(v, h);
-            if (lane < h) v = __fadd_rn(v, o);
-        }
-        return g.shfl(v, 0);
+        return node_sum_wide(alpha, A, len, mode, lane);
     }
 
-    // REP node of at most 4G values: S = sum alpha, and the penalties of the
+    // REP node of at most 32 values: S = sum alpha, and the penalties of the
     // all-zero and all-one words, each summed in halving order in one tree
     __device__ void rep_sums(int lam, float &S, float &pen0, float &pen1) const {
-        const int lane = g.lane;
         const int len = 1 << lam;
         const float *A = stage(lam);
-        float v, p0, p1;
-        if (len <= G) {
-            const float x = lane < len ? A[lane] : 0.0f;
-            v = x;
-            p0 = pen_transform(x, 1);
-            p1 = lane < len ? pen_transform(x, 2) : 0.0f;
-        } else {
-            float x[4];
-            x[0] = A[lane];
-            x[1] = A[lane + G];
-            x[2] = len == 4 * G ? A[lane + 2 * G] : 0.0f;
-            x[3] = len == 4 * G ? A[lane + 3 * G] : 0.0f;
-            float v1 = x[1], q0 = pen_transform(x[1], 1), q1 = pen_transform(x[1], 2);
-            v = x[0];
-            p0 = pen_transform(x[0], 1);
-            p1 = pen_transform(x[0], 2);
-            if (len == 4 * G) {
-                v = __fadd_rn(v, x[2]);
-                p0 = __fadd_rn(p0, pen_transform(x[2], 1));
-                p1 = __fadd_rn(p1, pen_transform(x[2], 2));
-                v1 = __fadd_rn(v1, x[3]);
-                q0 = __fadd_rn(q0, pen_transform(x[3], 1));
-                q1 = __fadd_rn(q1, pen_transform(x[3], 2));
-            }
-            v = __fadd_rn(v, v1);
-            p0 = __fadd_rn(p0, q0);
-            p1 = __fadd_rn(p1, q1);
-        }
-        for (int h = min(len, G) >> 1; h >= 1; h >>= 1) {
-            const float ov = g.shfl_down(v, h);
-            const float o0 = g.shfl_down(p0, h);
-            const float o1 = g.shfl_down(p1, h);
+        const float x = lane < len ? A[lane] : 0.0f;
+        float v = x, p0 = pen_transform(x, 1), p1 = lane < len ? pen_transform(x, 2) : 0.0f;
+        for (int h = len >> 1; h >= 1; h >>= 1) {
+            const float ov = __shfl_down_sync(FULL, v, h);
+            const float o0 = __shfl_down_sync(FULL, p0, h);
+            const float o1 = __shfl_down_sync(FULL, p1, h);
             if (lane < h) {
                 v = __fadd_rn(v, ov);
                 p0 = __fadd_rn(p0, o0);
                 p1 = __fadd_rn(p1, o1);
             }
         }
-        S = g.shfl(v, 0);
-        pen0 = g.shfl(p0, 0);
-        pen1 = g.shfl(p1, 0);
+        S = __shfl_sync(FULL, v, 0);
+        pen0 = __shfl_sync(FULL, p0, 0);
+        pen1 = __shfl_sync(FULL, p1, 0);
     }
 
     // the k least reliable positions (|alpha|, ties to the lower index)
     __device__ void node_least(int lam, int k, int *m, float *mag) const {
-        const int lane = g.lane;
         const int len = 1 << lam;
         const float *A = stage(lam);
-        if (len > 4 * G) {
-            const Least r = node_least_wide<G>(A, len, k, g);
+        if (len > 32) {
+            const Least r = node_least_wide(A, len, k, lane);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 m[j] = r.m[j];
@@ -629,37 +507,22 @@ struct Frame {
             }
             return;
         }
-        // up to 4 values a lane (positions lane + jG): k rounds of group minima
-        uint32_t v[4];
+        {  // one value per lane: k rounds of warp minima
+            uint32_t v = lane < len ? __float_as_uint(fabsf(A[lane])) : EMPTY;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = lane + q * G;
-            v[q] = i < len ? __float_as_uint(fabsf(A[i])) : EMPTY;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j >= k) break;
-            uint32_t bv = v[0];
-            int bq = 0;
-#pragma unroll
-            for (int q = 1; q < 4; ++q)
-                if (v[q] < bv) {
-                    bv = v[q];
-                    bq = q;
-                }
-            const uint32_t gv = g.rmin(bv);
-            const uint32_t gi = g.rmin(bv == gv ? uint32_t(lane + bq * G) : EMPTY);
-            m[j] = int(gi);
-            mag[j] = __uint_as_float(gv);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (uint32_t(lane + q * G) == gi) v[q] = EMPTY;
+            for (int j = 0; j < 4; ++j) {
+                if (j >= k) break;
+                const uint32_t gv = __reduce_min_sync(FULL, v);
+                const uint32_t gi = __reduce_min_sync(FULL, v == gv ? uint32_t(lane) : EMPTY);
+                m[j] = int(gi);
+                mag[j] = __uint_as_float(gv);
+                if (uint32_t(lane) == gi) v = EMPTY;
+            }
         }
     }
 
     // flip the candidate's positions relative to the node's hard decisions
     __device__ void apply_flips(uint32_t mask, const int *m, int s, int lam) const {
-        const int lane = g.lane;
         if (lam <= 5) {  // the node lies in one word: one masked XOR
             if (lane == 0 && mask) {
                 uint32_t x = (mask & FLIP_ALL) ? ((lam == 5) ? FULL : ((1u << (1 << lam)) - 1u)) : 0u;
@@ -668,14 +531,14 @@ struct Frame {
                     if ((mask >> j) & 1u) x ^= 1u << m[j];
                 beta[s >> 5] ^= x << (s & 31);
             }
-            g.sync();
+            __syncwarp();
             return;
         }
         if (mask & FLIP_ALL) {
             const int len = 1 << lam;
             if (len >= 32) {
                 #pragma unroll 1
-                for (int k = lane; k < (len >> 5); k += G) beta[(s >> 5) + k] ^= FULL;
+                for (int k = lane; k < (len >> 5); k += 32) beta[(s >> 5) + k] ^= FULL;
             } else if (lane == 0) {
                 beta[s >> 5] ^= ((1u << len) - 1u) << (s & 31);
             }
@@ -688,12 +551,12 @@ struct Frame {
                     beta[pos >> 5] ^= 1u << (pos & 31);
                 }
         }
-        g.sync();
+        __syncwarp();
     }
 };
 
-// The stack of one frame: entry j * G + lane lives in slot j of `lane`
-// (NS slots a lane hold NS * G entries).
+// The stack of one frame: entry j * 32 + lane lives in slot j of `lane`
+// (NS = 1 holds D <= 32 entries, NS = 2 up to 64).
 template <int NS>
 struct Stack {
     uint32_t pm[NS], meta[NS], seq[NS], aux[NS];  // meta = len | sched << 16
@@ -701,8 +564,7 @@ struct Stack {
 template <>
 struct Stack<0> {};  // the memory stack keeps nothing in registers
 
-template <int G>
-__device__ __forceinline__ bool slot_exists(int j, int lane, int D) { return j * G + lane < D; }
+__device__ __forceinline__ bool slot_exists(int j, int lane, int D) { return j * 32 + lane < D; }
 
 // Candidates of one expansion, described compactly so that every lane can
 // produce any candidate r from registers: flip mask r is nibble r of `masks`
@@ -730,27 +592,25 @@ struct Cands {
 // CRC syndrome of the codeword estimate in beta: zero iff the message's CRC
 // matches (the long division is linear, so the syndrome is a fixed GF(2)
 // matrix applied to the codeword bits)
-template <int G>
-__device__ __noinline__ bool crc_ok(const Code &c, const uint32_t *beta, Grp<G> g) {
+__device__ __noinline__ bool crc_ok(const Code &c, const uint32_t *beta, int lane) {
     uint32_t syn = 0u;
     for (int r = 0; r < c.crc; ++r) {
         uint32_t par = 0u;
         #pragma unroll 1
-        for (int k = g.lane; k < c.W; k += G) par ^= __popc(beta[k] & __ldg(c.crc_rows + size_t(r) * c.W + k));
+        for (int k = lane; k < c.W; k += 32) par ^= __popc(beta[k] & __ldg(c.crc_rows + size_t(r) * c.W + k));
         syn |= (par & 1u) << r;
     }
-    return g.rxor(syn) == 0u;
+    return __reduce_xor_sync(FULL, syn) == 0u;
 }
 
 // output: re-encode the codeword estimate (F is an involution, Sec. 2.2.2)
 // and read the message bits off the information set; a systematic code
 // carries them in the codeword estimate itself
-template <int G>
-__device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *orow, Grp<G> g) {
+__device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *orow, int lane) {
     const int W = c.W, N = c.N;
     if (!c.systematic) {
         #pragma unroll 1
-        for (int k = g.lane; k < W; k += G) {
+        for (int k = lane; k < W; k += 32) {
             uint32_t x = u[k];
             if (N > 1) x ^= (x >> 1) & 0x55555555u;
             if (N > 2) x ^= (x >> 2) & 0x33333333u;
@@ -759,16 +619,16 @@ __device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *
             if (N > 16) x ^= (x >> 16) & 0x0000FFFFu;
             u[k] = x;
         }
-        g.sync();
+        __syncwarp();
         for (int hw = 1; hw < W; hw <<= 1) {
             #pragma unroll 1
-            for (int k = g.lane; k < W; k += G)
+            for (int k = lane; k < W; k += 32)
                 if (!(k & hw)) u[k] ^= u[k + hw];
-            g.sync();
+            __syncwarp();
         }
     }
     #pragma unroll 1
-    for (int ow = g.lane; ow < c.info_words; ow += G) {
+    for (int ow = lane; ow < c.info_words; ow += 32) {
         uint32_t word = 0u;
         for (int bb = 0; bb < 32; ++bb) {
             const int j = ow * 32 + bb;
@@ -779,48 +639,31 @@ __device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *
         }
         orow[ow] = word;
     }
-    g.sync();
+    __syncwarp();
 }
 
 // ---- stack and snapshot bookkeeping (plain inline functions: the stack
 // stays in registers) ----
 
-// the worst entry a lane holds (largest pm, ties: oldest), over its slots
-template <int NS, int G>
-__device__ __forceinline__ void lane_worst(const Stack<NS> &st, int D, int lane, uint32_t &lw, uint32_t &ls, int &lj) {
-    const bool e0 = slot_exists<G>(0, lane, D);
-    lw = e0 ? st.pm[0] : 0u;
-    ls = e0 ? st.seq[0] : EMPTY;
-    lj = 0;
-#pragma unroll
-    for (int j = 1; j < NS; ++j)
-        if (slot_exists<G>(j, lane, D) && (st.pm[j] > lw || (st.pm[j] == lw && st.seq[j] < ls))) {
-            lw = st.pm[j];
-            ls = st.seq[j];
-            lj = j;
-        }
-}
-
 // insert candidates 0..nc-1 in order (reading R11): free slots first, all at
 // once, then one by one, each replacing the worst entry (largest pm, ties:
 // oldest) only if its pm is strictly smaller
-template <int NS, int G>
+template <int NS>
 __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Cands &c, float pm, uint32_t meta,
-                                             uint32_t base, uint32_t slot, int D, Grp<G> g) {
-    const int lane = g.lane;
+                                             uint32_t base, uint32_t slot, int D, int lane) {
     const int nfree = D - count;
     const int nb = c.nc < nfree ? c.nc : nfree;
-    // lane r forms candidate r's metric once (nc <= 8 <= G); the loops below read it
+    // lane r forms candidate r's metric once; the loops below read it
     const uint32_t my_pmb = __float_as_uint(__fadd_rn(pm, c.delta(lane < c.nc ? lane : 0)));
     if (nb > 0) {
         const uint32_t lt = (1u << lane) - 1u;
         int before = 0;  // free slots in the rows above
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-            const bool f = st.pm[j] == EMPTY && slot_exists<G>(j, lane, D);
-            const uint32_t bj = g.ballot(f);
+            const bool f = st.pm[j] == EMPTY && slot_exists(j, lane, D);
+            const uint32_t bj = __ballot_sync(FULL, f);
             const int r = before + __popc(bj & lt);
-            const uint32_t rpmb = g.shfl(my_pmb, r & (G - 1));
+            const uint32_t rpmb = __shfl_sync(FULL, my_pmb, r & 31);
             if (f && r < nb) {
                 st.pm[j] = rpmb;
                 st.meta[j] = meta;
@@ -839,24 +682,43 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
     bool stale = true;
     uint32_t todo = 0u;  // candidates below the worst entry (it only decreases)
     if (nb < c.nc) {
-        lane_worst<NS, G>(st, D, lane, lw, ls, lj);
-        gw = g.rmax(lw);
+        const bool e0 = slot_exists(0, lane, D);
+        lw = e0 ? st.pm[0] : 0u;
+        ls = e0 ? st.seq[0] : EMPTY;
+#pragma unroll
+        for (int j = 1; j < NS; ++j)
+            if (slot_exists(j, lane, D) && (st.pm[j] > lw || (st.pm[j] == lw && st.seq[j] < ls))) {
+                lw = st.pm[j];
+                ls = st.seq[j];
+                lj = j;
+            }
+        gw = __reduce_max_sync(FULL, lw);
         stale = false;
-        todo = g.ballot(lane >= nb && lane < c.nc && my_pmb < gw);
+        todo = __ballot_sync(FULL, lane >= nb && lane < c.nc && my_pmb < gw);
     }
     while (todo) {
         const int k = __ffs(todo) - 1;
         todo &= todo - 1u;
-        const uint32_t pmb = g.shfl(my_pmb, k);
+        const uint32_t pmb = __shfl_sync(FULL, my_pmb, k);
         if (stale) {
-            lane_worst<NS, G>(st, D, lane, lw, ls, lj);
-            gw = g.rmax(lw);
+            const bool e0 = slot_exists(0, lane, D);
+            lw = e0 ? st.pm[0] : 0u;
+            ls = e0 ? st.seq[0] : EMPTY;
+            lj = 0;
+#pragma unroll
+            for (int j = 1; j < NS; ++j)
+                if (slot_exists(j, lane, D) && (st.pm[j] > lw || (st.pm[j] == lw && st.seq[j] < ls))) {
+                    lw = st.pm[j];
+                    ls = st.seq[j];
+                    lj = j;
+                }
+            gw = __reduce_max_sync(FULL, lw);
             stale = false;
         }
         if (pmb < gw) {
             stale = true;
-            const uint32_t gs = g.rmin(lw == gw ? ls : EMPTY);
-            const uint32_t bal = g.ballot(lw == gw && ls == gs);
+            const uint32_t gs = __reduce_min_sync(FULL, lw == gw ? ls : EMPTY);
+            const uint32_t bal = __ballot_sync(FULL, lw == gw && ls == gs);
             if (lane == __ffs(bal) - 1) {
 #pragma unroll
                 for (int j = 0; j < NS; ++j)
@@ -873,16 +735,13 @@ __device__ __forceinline__ void insert_cands(Stack<NS> &st, int &count, const Ca
 
 // a free snapshot slot among 0 .. D-1 (one always exists: the extended path
 // left the stack, so at most D - 1 snapshots are referenced)
-template <int NS, int G>
-__device__ __forceinline__ int alloc_snapshot(const Stack<NS> &st, int D, Grp<G> g) {
-    if (D <= 32) {  // slot ids below 32: one word
+template <int NS>
+__device__ __forceinline__ int alloc_snapshot(const Stack<NS> &st, int D) {
+    if constexpr (NS == 1) {  // D <= 32: slot ids below 32, one word
         uint32_t used = 0u;
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-            const uint32_t sn = st.aux[j] & 0xFFu;
-            if (st.pm[j] != EMPTY && sn < 32u) used |= 1u << sn;
-        }
-        used = g.ror(used);
+        const uint32_t sn = st.aux[0] & 0xFFu;
+        if (st.pm[0] != EMPTY && sn < 32u) used = 1u << sn;
+        used = __reduce_or_sync(FULL, used);
         const uint32_t fr = ~used & (D >= 32 ? FULL : ((1u << D) - 1u));
         return fr ? (__ffs(int(fr)) - 1) : -1;
     }
@@ -895,28 +754,27 @@ __device__ __forceinline__ int alloc_snapshot(const Stack<NS> &st, int D, Grp<G>
             else if (sn < 64u) hi |= 1u << (sn - 32u);
         }
     }
-    lo = g.ror(lo);
-    hi = g.ror(hi);
+    lo = __reduce_or_sync(FULL, lo);
+    hi = __reduce_or_sync(FULL, hi);
     const uint64_t used = (uint64_t(hi) << 32) | uint64_t(lo);
     const uint64_t all = (D >= 64) ? ~0ull : ((1ull << D) - 1ull);
     const uint64_t fr = ~used & all;
     return fr ? (__ffsll((long long)fr) - 1) : -1;
 }
 
-template <int G>
-__device__ __forceinline__ void write_snapshot(const Frame<G> &w, int W, int SW, int slot, int nbits, uint32_t m01,
+__device__ __forceinline__ void write_snapshot(const Warp &w, int W, int SW, int slot, int nbits, uint32_t m01,
                                                uint32_t m23, int s, int lam) {
     uint32_t *sp = w.scr + size_t(slot) * SW;
     const int nw = min(W, (nbits + 31) >> 5);
     #pragma unroll 1
-    for (int k = w.g.lane; k < nw; k += G) sp[k] = w.beta[k];
-    if (w.g.lane == 0) {
+    for (int k = w.lane; k < nw; k += 32) sp[k] = w.beta[k];
+    if (w.lane == 0) {
         sp[W] = m01;
         sp[W + 1] = m23;
         sp[W + 2] = uint32_t(s);
         sp[W + 3] = uint32_t(lam);
     }
-    w.g.sync();
+    __syncwarp();
 }
 
 // ---- the memory stack (depths above 64, e.g. the D = 8192 of Sec. 5) ----
@@ -1076,514 +934,436 @@ __device__ __noinline__ int mem_prune(MemStack ms, int count, int s, int lane) {
     return out;
 }
 
-// The search state of one frame, held in its group's registers between
-// iterations: the stack (NS >= 1: the register stack of D <= NS * G entries;
-// NS = 0: the memory stack `ms`, whole warps), the bookkeeping of the
-// working path and the counters.
-template <int G, int NS>
-struct Search {
-    Stack<NS> st;
-    MemStack ms;
-    int D, L, max_iter, first_slot, iter, count;
-    uint32_t stack_cost, seq_next, ops, n_iter, n_switch, n_exp;
-    uint32_t cur_snap;  // snapshot of the latest expansion
-    uint32_t applied;   // flips applied on top of the latest snapshot
-    bool beta_dirty;    // working beta replaced since that expansion
-    bool have_first;
-    int cm[4];
-    int cs, clam;       // node of the latest expansion
-    // alpha stages valid_lo .. n-1 hold the spine of node (clam, cs),
-    // computed from the working beta's prefix (n: none valid)
-    int cur_lo, valid_lo;
-    int crc_fails;
-    float first_pm, out_pm;
-    int status;
-    int out_src;  // 0: zeros, 1: working beta, 2: first complete path
-#ifdef POLAR_PHASE_TIMERS
-    unsigned long long pt_acc[PH_N];
-#endif
-};
-
-// a new frame: zero the visit counters and beta, push the initial path
-template <int G, int NS>
-__device__ __forceinline__ void search_init(Search<G, NS> &S, const Code &c, int D, int L, const Frame<G> &w,
-                                            const MemStack ms) {
+// NS = 1, 2: the register stack (D <= 32, 64); NS = 0: the memory stack `ms`
+template <int NS, bool EXACT, bool STATS>
+__device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Warp &w,
+                                             unsigned b, uint32_t *orow, const MemStack ms) {
     constexpr bool DEEP = NS == 0;
-    static_assert(!DEEP || G == 32, "the memory stack runs on whole warps");
-    const Grp<G> g = w.g;
-    const int lane = g.lane;
-    S.ms = ms;
-    S.D = D;
-    S.L = L;
-    S.max_iter = L * (c.nbranch + 9) + 2;
+    constexpr uint32_t nosnap = DEEP ? NOSNAP_DEEP : NOSNAP;
+    constexpr int mask_shift = DEEP ? 24 : 8;
+    const int lane = w.lane;
+    const int N = c.N, W = c.W, n = c.n;
+    const int SW = c.snap_words;
+    const int max_iter = L * (c.nbranch + 9) + 2;
     // snapshot slots: 0 .. D-1 reused (register stack) or one per iteration
     // (memory stack); the slot after them keeps the first complete path
-    S.first_slot = DEEP ? S.max_iter : D;
-    S.stack_cost = 2u * uint32_t(D > 2 ? 32 - __clz(D - 1) : 1);
+    const int first_slot = DEEP ? max_iter : D;
+    const uint32_t stack_cost = 2u * uint32_t(D > 2 ? 32 - __clz(D - 1) : 1);
+
+    PT_INIT
     #pragma unroll 1
-    for (int i = lane; i < c.nbranch; i += G) w.cnt[i] = 0;
+    for (int i = lane; i < c.nbranch; i += 32) w.cnt[i] = 0;
     #pragma unroll 1
-    for (int i = lane; i < c.W; i += G) w.beta[i] = 0u;
-    g.sync();
+    for (int i = lane; i < W; i += 32) w.beta[i] = 0u;
+    __syncwarp();
+
+    Stack<NS> st;
     if constexpr (DEEP) {
         if (lane == 0) {  // the initial path: pm 0, length 0, schedule 0
             ms.e[0] = make_uint4(__float_as_uint(0.0f), 0u, 0u, NOSNAP_DEEP);
             ms.best[0] = make_uint2(__float_as_uint(0.0f), 0u);
         }
-        g.sync();
+        __syncwarp();
     } else {
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-            S.st.pm[j] = EMPTY;
-            S.st.meta[j] = 0u;
-            S.st.seq[j] = 0u;
-            S.st.aux[j] = NOSNAP;
+            st.pm[j] = EMPTY;
+            st.meta[j] = 0u;
+            st.seq[j] = 0u;
+            st.aux[j] = NOSNAP;
         }
         if (lane == 0) {  // the initial path: pm 0, length 0, schedule 0
-            S.st.pm[0] = __float_as_uint(0.0f);
-            S.st.meta[0] = 0u;
-            S.st.seq[0] = 0u;
-            S.st.aux[0] = NOSNAP;
+            st.pm[0] = __float_as_uint(0.0f);
+            st.meta[0] = 0u;
+            st.seq[0] = 0u;
+            st.aux[0] = NOSNAP;
         }
     }
-    S.iter = 0;
-    S.count = 1;
-    S.seq_next = 1;
-    S.ops = S.stack_cost;  // counted operations (roofline convention)
-    S.n_iter = S.n_switch = S.n_exp = 0;
-    S.cur_snap = DEEP ? NOSNAP_DEEP : NOSNAP;
-    S.applied = 0;
-    S.beta_dirty = false;
-    S.have_first = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) S.cm[j] = 0;
-    S.cs = 0;
-    S.clam = c.n;
-    S.cur_lo = S.valid_lo = c.n;
-    S.crc_fails = 0;
-    S.first_pm = 0.0f;
-    S.status = POLAR_TIMEOUT;
-    S.out_pm = __int_as_float(0x7f800000);
-    S.out_src = 0;
-#ifdef POLAR_PHASE_TIMERS
-    for (int q = 0; q < PH_N; ++q) S.pt_acc[q] = 0ull;
-#endif
-}
+    int count = 1;
+    uint32_t seq_next = 1;
+    uint32_t ops = stack_cost;  // counted operations (roofline convention)
+    uint32_t n_iter = 0, n_switch = 0, n_exp = 0;
 
-// One iteration of the search (Sec. 2.2.5): pop the best path, restore it,
-// walk the schedule to its next branching node and push the candidates.
-// Returns true once the frame's result is decided (S.status, S.out_src).
-template <int G, int NS, bool EXACT, bool STATS>
-__device__ __forceinline__ bool search_step(Search<G, NS> &S, const Code &c, const Frame<G> &w) {
-    constexpr bool DEEP = NS == 0;
-    constexpr uint32_t nosnap = DEEP ? NOSNAP_DEEP : NOSNAP;
-    constexpr int mask_shift = DEEP ? 24 : 8;
-    const Grp<G> g = w.g;
-    const int lane = g.lane;
-    const int N = c.N, W = c.W, n = c.n;
-    const int SW = c.snap_words;
-    const int D = S.D, L = S.L;
-    const MemStack ms = S.ms;
-    if (S.iter >= S.max_iter) return true;  // iteration guard: status stays TIMEOUT
-#ifdef POLAR_PHASE_TIMERS
-    long long pt_t = clock64();
-#define PTS(ph) { const long long pt_n = clock64(); S.pt_acc[ph] += (unsigned long long)(pt_n - pt_t); pt_t = pt_n; }
-#else
-#define PTS(ph)
-#endif
-    if (S.count == 0) {  // every path deleted (reading R12)
-        S.status = POLAR_CRC_FAIL;
-        if (S.have_first) {
-            S.out_pm = S.first_pm;
-            S.out_src = 2;
-        }
-        return true;
-    }
-    // ---- pop the best path: smallest pm, ties to the newest ----
-    uint32_t p_pmb, p_meta, p_aux;
-    if constexpr (DEEP) {
-        const Popped pp = mem_pop(ms, S.count, lane);
-        if (!pp.ok) {  // count out of step with the entries: stop safely
-            S.status = POLAR_TIMEOUT;
-            return true;
-        }
-        p_pmb = pp.pmb;
-        p_meta = pp.meta;
-        p_aux = pp.aux;
-    } else {
-        uint32_t lp = S.st.pm[0], ls = S.st.seq[0];
-        int lj = 0;
-#pragma unroll
-        for (int j = 1; j < NS; ++j)
-            if (S.st.pm[j] < lp || (S.st.pm[j] == lp && S.st.pm[j] != EMPTY && S.st.seq[j] > ls)) {
-                lp = S.st.pm[j];
-                ls = S.st.seq[j];
-                lj = j;
+    uint32_t cur_snap = nosnap;  // snapshot of the latest expansion
+    bool beta_dirty = false;     // working beta replaced since that expansion
+    uint32_t applied = 0;        // flips applied on top of the latest snapshot
+    int cm[4] = {0, 0, 0, 0};
+    int cs = 0, clam = n;        // node of the latest expansion
+    // alpha stages valid_lo .. n-1 hold the spine of node (clam, cs),
+    // computed from the working beta's prefix (n: none valid)
+    int cur_lo = n, valid_lo = n;
+
+    int crc_fails = 0;
+    bool have_first = false;
+    float first_pm = 0.0f;
+    int status = POLAR_TIMEOUT;
+    float out_pm = __int_as_float(0x7f800000);
+    int out_src = 0;  // 0: zeros, 1: working beta, 2: first complete path
+
+    int iter = 0;
+    for (; iter < max_iter; ++iter) {
+        if (count == 0) {  // every path deleted (reading R12)
+            status = POLAR_CRC_FAIL;
+            if (have_first) {
+                out_pm = first_pm;
+                out_src = 2;
             }
-        const uint32_t gp = g.rmin(lp);
-        if (gp == EMPTY) {  // count out of step with the slots: stop safely
-            S.status = POLAR_TIMEOUT;
-            return true;
+            break;
         }
-        const uint32_t gs = g.rmax(lp == gp ? ls : 0u);
-        const uint32_t bal = g.ballot(lp == gp && ls == gs);
-        const int wl = __ffs(bal) - 1;
-        p_pmb = gp;
-        uint32_t my_meta = S.st.meta[0], my_aux = S.st.aux[0];  // this lane's best entry
-#pragma unroll
-        for (int j = 1; j < NS; ++j)
-            if (lj == j) {
-                my_meta = S.st.meta[j];
-                my_aux = S.st.aux[j];
+        // ---- pop the best path: smallest pm, ties to the newest ----
+        uint32_t p_pmb, p_meta, p_aux;
+        if constexpr (DEEP) {
+            const Popped pp = mem_pop(ms, count, lane);
+            if (!pp.ok) {  // count out of step with the entries: stop safely
+                status = POLAR_TIMEOUT;
+                break;
             }
-        p_meta = g.shfl(my_meta, wl);
-        p_aux = g.shfl(my_aux, wl);
-        if (lane == wl) {
-#pragma unroll
-            for (int j = 0; j < NS; ++j)
-                if (lj == j) S.st.pm[j] = EMPTY;
-        }
-    }
-    --S.count;
-    ++S.n_iter;
-    S.ops += S.stack_cost;
-    const int p_sched = int(p_meta >> 16);
-    const uint32_t p_snap = p_aux & nosnap;
-    const uint32_t p_mask = (p_aux >> mask_shift) & 0x1Fu;
-    if (p_snap != nosnap && p_snap >= uint32_t(S.first_slot)) {  // never produced; guards the scratch index
-        S.status = POLAR_TIMEOUT;
-        return true;
-    }
-    if (p_sched > c.nops) {
-        S.status = POLAR_TIMEOUT;
-        return true;
-    }
-    PTS(PH_POP)
-
-    // ---- restore the path's beta array ----
-    bool switched = false;
-    int div = 0;  // first bit where the popped path's beta differs from the working one
-    if (p_snap == S.cur_snap) {
-        if (S.beta_dirty) {
-            const uint32_t *sp = w.scr + size_t(S.cur_snap) * SW;
-            #pragma unroll 1
-            for (int k = lane; k < W; k += G) w.beta[k] = sp[k];
-            g.sync();
-            S.applied = 0u;
-            S.beta_dirty = false;
-            S.valid_lo = S.cur_lo;
-        }
-        w.apply_flips(S.applied ^ p_mask, S.cm, S.cs, S.clam);
-        S.applied = p_mask;
-    } else {  // path switch (Sec. 3.3)
-        switched = true;
-        ++S.n_switch;
-        S.ops += uint32_t(W);
-        div = restore_switch<G>(w.scr + size_t(p_snap) * SW, w.beta, W, p_mask, g);
-        S.beta_dirty = true;
-    }
-    PTS(PH_BETA)
-
-    if (p_sched == c.nops) {  // a complete path
-        if (switched) S.valid_lo = n;  // beta replaced, alpha left as it was
-        bool pass = true;
-        if (c.crc) {
-            S.ops += uint32_t(c.crc) * uint32_t(W);
-            pass = crc_ok<G>(c, w.beta, g);
-        }
-        if (pass) {
-            S.status = POLAR_OK;
-            S.out_pm = __uint_as_float(p_pmb);
-            S.out_src = 1;
-            return true;
-        }
-        ++S.crc_fails;
-        if (!S.have_first) {
-            S.have_first = true;
-            S.first_pm = __uint_as_float(p_pmb);
-            uint32_t *sp = w.scr + size_t(S.first_slot) * SW;
-            #pragma unroll 1
-            for (int k = lane; k < W; k += G) sp[k] = w.beta[k];
-            g.sync();
-        }
-        if (S.crc_fails >= L) {
-            S.status = POLAR_CRC_FAIL;
-            S.out_pm = S.first_pm;
-            S.out_src = 2;
-            return true;
-        }
-        PTS(PH_DONE)
-        ++S.iter;
-        return false;
-    }
-
-    // ---- alpha after a switch (Alg. calp): recompute the spine from the
-    // channel, except the top stages the popped path shares with the
-    // spine held now (same node, identical beta before the node).  The
-    // recomputed stages rl .. lam_d run through the same op dispatch as
-    // the schedule walk below. ----
-    int rl = -1, lam_d = 0, s_d = 0;
-    if (switched) {
-        const uint32_t tgt = __ldg(&c.ops[p_sched].z);
-        if (tgt != NO_TARGET) {
-            lam_d = int(tgt & 0xFFu);
-            s_d = int(tgt >> 8);
-            S.ops += 2u * uint32_t(N - (1 << lam_d));  // counted as the full recompute
-            int lam = n - 1;
-            while (lam >= lam_d && lam >= S.valid_lo && (s_d >> lam) == (S.cs >> lam) &&
-                   div >= ((s_d >> lam) << lam))
-                --lam;
-            rl = lam;
-        }
-    }
-    PTS(PH_ALPHA)
-
-    // ---- walk the schedule to the next branching node (Sec. 4) ----
-    float pm = __uint_as_float(p_pmb);
-    int t = p_sched;
-    const uint4 *opsv = reinterpret_cast<const uint4 *>(c.ops);
-    uint4 nxt = __ldg(opsv + min(t, c.nops - 1));
-    uint4 op = nxt;
-    for (;;) {
-        uint32_t code;
-        int lam, s, run = 1;
-        const bool sched = rl < lam_d;  // else: a recomputed spine stage
-        if (!sched) {
-            lam = rl;
-            s = (s_d >> lam) << lam;
-            code = ((s_d >> lam) & 1) ? OP_G : OP_F;
-            --rl;
+            p_pmb = pp.pmb;
+            p_meta = pp.meta;
+            p_aux = pp.aux;
         } else {
-            if (t >= c.nops) break;
-            op = nxt;
-            if (t + 1 < c.nops) nxt = __ldg(opsv + t + 1);
-            code = op.x & 0xFFu;
-            lam = int((op.x >> 8) & 0xFFu);
-            s = int(op.y);
-            run = int((op.x >> 16) & 0xFFu) + 1;
-            if (code >= OP_BRANCH) break;
-            ++t;
-        }
-        if (code <= OP_G) {  // an F or G, then run - 1 F ops down the left edge
-            #pragma unroll 1
-            for (int i = 0; i < run; ++i) {
-                if (i == 0 && code == OP_G) w.op_g(lam, s);
-                else w.template op_f<EXACT>(lam - i);
-                if (sched) S.ops += 2u << (lam - i);
-            }
-            PTS(PH_FG)
-        } else if (code == OP_COMB) {  // run combines, one stage up each
-            #pragma unroll 1
-            for (int i = 0; i < run; ++i) {
-                w.op_comb(lam + i, s);
-                S.ops += (lam + i < 5) ? 1u : (1u << (lam + i - 5));
-                s -= 1 << (lam + i);
-            }
-            PTS(PH_COMB)
-        } else {  // Rate-0 node or frozen leaf: beta = 0, PM += sum HD(a)|a|
-            const float pen = w.node_sum(lam, EXACT ? 3 : 1);
-            w.set_range(lam, s, 0u);
-            pm = __fadd_rn(pm, pen);
-            S.ops += (2u << lam) + 1u;
-            PTS(PH_R0)
-        }
-    }
-    ++S.n_exp;
-
-    // ---- the expansion's candidates: a complete path is pushed as it
-    // is; a branching node gets its visit counter, the L-prune
-    // (Sec. 2.2.5) and the node candidates (Sec. 2.2.4, readings R7-R9) ----
-    Cands cd{0, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
-    int m[4] = {0, 0, 0, 0};
-    int node_s = 0, node_lam = n, snap_lam = 0, nbits = N;
-    uint32_t meta = uint32_t(N) | (uint32_t(c.nops) << 16);
-    if (t >= c.nops) {
-        cd.nc = 1;
-        S.ops += 1u;
-    } else {
-        const uint32_t code = op.x & 0xFFu;
-        const int lam = int((op.x >> 8) & 0xFFu);
-        const int s = int(op.y);
-        const int len = 1 << lam;
-        node_s = s;
-        node_lam = snap_lam = lam;
-        nbits = s + len;
-        meta = uint32_t(s + len) | (uint32_t(t + 1) << 16);
-        uint32_t vc = 0;
-        if (lane == 0) vc = ++w.cnt[op.w];
-        vc = g.shfl(vc, 0);
-        g.sync();
-        if (int(vc) >= L) {
-            S.ops += S.stack_cost;
-            if constexpr (DEEP) {
-                S.count = mem_prune(ms, S.count, s, lane);
-            } else {
-                int removed = 0;
+            uint32_t lp = st.pm[0], ls = st.seq[0];
+            int lj = 0;
 #pragma unroll
-                for (int j = 0; j < NS; ++j) {
-                    const bool kill = S.st.pm[j] != EMPTY && int(S.st.meta[j] & 0xFFFFu) <= s;
-                    removed += __popc(g.ballot(kill));
-                    if (kill) S.st.pm[j] = EMPTY;
+            for (int j = 1; j < NS; ++j)
+                if (st.pm[j] < lp || (st.pm[j] == lp && st.pm[j] != EMPTY && st.seq[j] > ls)) {
+                    lp = st.pm[j];
+                    ls = st.seq[j];
+                    lj = j;
                 }
-                S.count -= removed;
+            const uint32_t gp = __reduce_min_sync(FULL, lp);
+            if (gp == EMPTY) {  // count out of step with the slots: stop safely
+                status = POLAR_TIMEOUT;
+                break;
+            }
+            const uint32_t gs = __reduce_max_sync(FULL, lp == gp ? ls : 0u);
+            const uint32_t bal = __ballot_sync(FULL, lp == gp && ls == gs);
+            const int wl = __ffs(bal) - 1;
+            p_pmb = gp;
+            uint32_t my_meta = st.meta[0], my_aux = st.aux[0];  // this lane's best entry
+#pragma unroll
+            for (int j = 1; j < NS; ++j)
+                if (lj == j) {
+                    my_meta = st.meta[j];
+                    my_aux = st.aux[j];
+                }
+            p_meta = __shfl_sync(FULL, my_meta, wl);
+            p_aux = __shfl_sync(FULL, my_aux, wl);
+            if (lane == wl) {
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    if (lj == j) st.pm[j] = EMPTY;
             }
         }
-        PTS(PH_PRUNE)
+        --count;
+        ++n_iter;
+        ops += stack_cost;
+        const int p_sched = int(p_meta >> 16);
+        const uint32_t p_snap = p_aux & nosnap;
+        const uint32_t p_mask = (p_aux >> mask_shift) & 0x1Fu;
+        if (p_snap != nosnap && p_snap >= uint32_t(first_slot)) {  // never produced; guards the scratch index
+            status = POLAR_TIMEOUT;
+            break;
+        }
+        if (p_sched > c.nops) {
+            status = POLAR_TIMEOUT;
+            break;
+        }
+        PT(PH_POP)
 
-        if (code == OP_REP) {
-            float Sv, p0;
-            uint32_t bbit;
-            if (len <= 4 * G) {
-                float pz, po;
-                w.rep_sums(lam, Sv, pz, po);
-                bbit = Sv < 0.0f ? 1u : 0u;
-                p0 = bbit ? po : pz;
-            } else {
-                Sv = w.node_sum(lam, 0);
-                bbit = Sv < 0.0f ? 1u : 0u;
-                p0 = w.node_sum(lam, bbit ? 2 : 1);
+        // ---- restore the path's beta array ----
+        bool switched = false;
+        int div = 0;  // first bit where the popped path's beta differs from the working one
+        if (p_snap == cur_snap) {
+            if (beta_dirty) {
+                const uint32_t *sp = w.scr + size_t(cur_snap) * SW;
+                #pragma unroll 1
+                for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
+                __syncwarp();
+                applied = 0u;
+                beta_dirty = false;
+                valid_lo = cur_lo;
             }
-            w.set_range(lam, s, bbit);
-            cd.nc = 2;
-            cd.rep = true;
-            cd.rep0 = p0;
-            cd.rep1 = __fadd_rn(p0, fabsf(Sv));
-            S.ops += 4u * uint32_t(len) + 3u;
-        } else {  // information leaf, Rate-1 or SPC: hard decisions first
-            const uint32_t q = w.node_hd(lam, s);
-            if (code == OP_LEAF1 && EXACT) {  // ln(1 + e^-|a|), ln(1 + e^|a|)
-                const float aa = fabsf(w.stage(0)[0]);
+            w.apply_flips(applied ^ p_mask, cm, cs, clam);
+            applied = p_mask;
+        } else {  // path switch (Sec. 3.3)
+            switched = true;
+            ++n_switch;
+            ops += uint32_t(W);
+            div = restore_switch(w.scr + size_t(p_snap) * SW, w.beta, W, p_mask, lane);
+            beta_dirty = true;
+        }
+        PT(PH_BETA)
+
+        if (p_sched == c.nops) {  // a complete path
+            if (switched) valid_lo = n;  // beta replaced, alpha left as it was
+            bool pass = true;
+            if (c.crc) {
+                ops += uint32_t(c.crc) * uint32_t(W);
+                pass = crc_ok(c, w.beta, lane);
+            }
+            if (pass) {
+                status = POLAR_OK;
+                out_pm = __uint_as_float(p_pmb);
+                out_src = 1;
+                break;
+            }
+            ++crc_fails;
+            if (!have_first) {
+                have_first = true;
+                first_pm = __uint_as_float(p_pmb);
+                uint32_t *sp = w.scr + size_t(first_slot) * SW;
+                #pragma unroll 1
+                for (int k = lane; k < W; k += 32) sp[k] = w.beta[k];
+                __syncwarp();
+            }
+            if (crc_fails >= L) {
+                status = POLAR_CRC_FAIL;
+                out_pm = first_pm;
+                out_src = 2;
+                break;
+            }
+            PT(PH_DONE)
+            continue;
+        }
+
+        // ---- alpha after a switch (Alg. calp): recompute the spine from the
+        // channel, except the top stages the popped path shares with the
+        // spine held now (same node, identical beta before the node).  The
+        // recomputed stages rl .. lam_d run through the same op dispatch as
+        // the schedule walk below. ----
+        int rl = -1, lam_d = 0, s_d = 0;
+        if (switched) {
+            const uint32_t tgt = __ldg(&c.ops[p_sched].z);
+            if (tgt != NO_TARGET) {
+                lam_d = int(tgt & 0xFFu);
+                s_d = int(tgt >> 8);
+                ops += 2u * uint32_t(N - (1 << lam_d));  // counted as the full recompute
+                int lam = n - 1;
+                while (lam >= lam_d && lam >= valid_lo && (s_d >> lam) == (cs >> lam) && div >= ((s_d >> lam) << lam))
+                    --lam;
+                rl = lam;
+            }
+        }
+        PT(PH_ALPHA)
+
+        // ---- walk the schedule to the next branching node (Sec. 4) ----
+        float pm = __uint_as_float(p_pmb);
+        int t = p_sched;
+        const uint4 *opsv = reinterpret_cast<const uint4 *>(c.ops);
+        uint4 nxt = __ldg(opsv + min(t, c.nops - 1));
+        uint4 op = nxt;
+        for (;;) {
+            uint32_t code;
+            int lam, s, run = 1;
+            const bool sched = rl < lam_d;  // else: a recomputed spine stage
+            if (!sched) {
+                lam = rl;
+                s = (s_d >> lam) << lam;
+                code = ((s_d >> lam) & 1) ? OP_G : OP_F;
+                --rl;
+            } else {
+                if (t >= c.nops) break;
+                op = nxt;
+                if (t + 1 < c.nops) nxt = __ldg(opsv + t + 1);
+                code = op.x & 0xFFu;
+                lam = int((op.x >> 8) & 0xFFu);
+                s = int(op.y);
+                run = int((op.x >> 16) & 0xFFu) + 1;
+                if (code >= OP_BRANCH) break;
+                ++t;
+            }
+            if (code <= OP_G) {  // an F or G, then run - 1 F ops down the left edge
+                #pragma unroll 1
+                for (int i = 0; i < run; ++i) {
+                    if (i == 0 && code == OP_G) w.op_g(lam, s);
+                    else w.template op_f<EXACT>(lam - i);
+                    if (sched) ops += 2u << (lam - i);
+                }
+                PT(PH_FG)
+            } else if (code == OP_COMB) {  // run combines, one stage up each
+                #pragma unroll 1
+                for (int i = 0; i < run; ++i) {
+                    w.op_comb(lam + i, s);
+                    ops += (lam + i < 5) ? 1u : (1u << (lam + i - 5));
+                    s -= 1 << (lam + i);
+                }
+                PT(PH_COMB)
+            } else {  // Rate-0 node or frozen leaf: beta = 0, PM += sum HD(a)|a|
+                const float pen = w.node_sum(lam, EXACT ? 3 : 1);
+                w.set_range(lam, s, 0u);
+                pm = __fadd_rn(pm, pen);
+                ops += (2u << lam) + 1u;
+                PT(PH_R0)
+            }
+        }
+        ++n_exp;
+
+        // ---- the expansion's candidates: a complete path is pushed as it
+        // is; a branching node gets its visit counter, the L-prune
+        // (Sec. 2.2.5) and the node candidates (Sec. 2.2.4, readings R7-R9) ----
+        Cands cd{0, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
+        int m[4] = {0, 0, 0, 0};
+        int node_s = 0, node_lam = n, snap_lam = 0, nbits = N;
+        uint32_t meta = uint32_t(N) | (uint32_t(c.nops) << 16);
+        if (t >= c.nops) {
+            cd.nc = 1;
+            ops += 1u;
+        } else {
+            const uint32_t code = op.x & 0xFFu;
+            const int lam = int((op.x >> 8) & 0xFFu);
+            const int s = int(op.y);
+            const int len = 1 << lam;
+            node_s = s;
+            node_lam = snap_lam = lam;
+            nbits = s + len;
+            meta = uint32_t(s + len) | (uint32_t(t + 1) << 16);
+            uint32_t vc = 0;
+            if (lane == 0) vc = ++w.cnt[op.w];
+            vc = __shfl_sync(FULL, vc, 0);
+            __syncwarp();
+            if (int(vc) >= L) {
+                ops += stack_cost;
+                if constexpr (DEEP) {
+                    count = mem_prune(ms, count, s, lane);
+                } else {
+                    int removed = 0;
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) {
+                        const bool kill = st.pm[j] != EMPTY && int(st.meta[j] & 0xFFFFu) <= s;
+                        removed += __popc(__ballot_sync(FULL, kill));
+                        if (kill) st.pm[j] = EMPTY;
+                    }
+                    count -= removed;
+                }
+            }
+            PT(PH_PRUNE)
+
+            if (code == OP_REP) {
+                float S, p0;
+                uint32_t bbit;
+                if (len <= 32) {
+                    float pz, po;
+                    w.rep_sums(lam, S, pz, po);
+                    bbit = S < 0.0f ? 1u : 0u;
+                    p0 = bbit ? po : pz;
+                } else {
+                    S = w.node_sum(lam, 0);
+                    bbit = S < 0.0f ? 1u : 0u;
+                    p0 = w.node_sum(lam, bbit ? 2 : 1);
+                }
+                w.set_range(lam, s, bbit);
                 cd.nc = 2;
                 cd.rep = true;
-                cd.rep0 = softplus_f(-aa);
-                cd.rep1 = softplus_f(aa);
-                S.ops += 4u;
-            } else if (code == OP_LEAF1) {
-                cd.mag[0] = fabsf(w.stage(0)[0]);
-                cd.nc = 2;
-                cd.masks = LEAF1_MASKS;
-                S.ops += 4u;
-            } else {
-                const bool spc = code == OP_SPC;
-                w.node_least(lam, spc ? 4 : 2, m, cd.mag);
-                cd.nc = spc ? 8 : 4;
-                cd.masks = spc ? (q ? SPC_MASKS_ODD : SPC_MASKS_EVEN) : R1_MASKS;
-                S.ops += spc ? 10u * uint32_t(len) + (q ? 16u : 17u) : 6u * uint32_t(len) + 5u;
+                cd.rep0 = p0;
+                cd.rep1 = __fadd_rn(p0, fabsf(S));
+                ops += 4u * uint32_t(len) + 3u;
+            } else {  // information leaf, Rate-1 or SPC: hard decisions first
+                const uint32_t q = w.node_hd(lam, s);
+                if (code == OP_LEAF1 && EXACT) {  // ln(1 + e^-|a|), ln(1 + e^|a|)
+                    const float aa = fabsf(w.stage(0)[0]);
+                    cd.nc = 2;
+                    cd.rep = true;
+                    cd.rep0 = softplus_f(-aa);
+                    cd.rep1 = softplus_f(aa);
+                    ops += 4u;
+                } else if (code == OP_LEAF1) {
+                    cd.mag[0] = fabsf(w.stage(0)[0]);
+                    cd.nc = 2;
+                    cd.masks = LEAF1_MASKS;
+                    ops += 4u;
+                } else {
+                    const bool spc = code == OP_SPC;
+                    w.node_least(lam, spc ? 4 : 2, m, cd.mag);
+                    cd.nc = spc ? 8 : 4;
+                    cd.masks = spc ? (q ? SPC_MASKS_ODD : SPC_MASKS_EVEN) : R1_MASKS;
+                    ops += spc ? 10u * uint32_t(len) + (q ? 16u : 17u) : 6u * uint32_t(len) + 5u;
+                }
             }
+            PT(PH_NODE)
         }
-        PTS(PH_NODE)
+
+        int slot;
+        if constexpr (DEEP) slot = iter;  // one slot per iteration, never reused
+        else slot = alloc_snapshot(st, D);
+        if (slot < 0) break;
+        write_snapshot(w, W, SW, slot, nbits, uint32_t(m[0]) | (uint32_t(m[1]) << 16),
+                       uint32_t(m[2]) | (uint32_t(m[3]) << 16), node_s, snap_lam);
+        cur_snap = uint32_t(slot);
+        applied = 0u;
+        beta_dirty = false;
+        cm[0] = m[0];
+        cm[1] = m[1];
+        cm[2] = m[2];
+        cm[3] = m[3];
+        cs = node_s;
+        clam = node_lam;
+        cur_lo = valid_lo = node_lam;
+        PT(PH_SNAP)
+        ops += uint32_t(cd.nc) * stack_cost;
+        if constexpr (DEEP) {
+            count = mem_insert(ms, count, cd, pm, meta, seq_next, uint32_t(slot), D, lane);
+            if (count < 0) {  // the entry region is full (excluded by its sizing)
+                status = POLAR_TIMEOUT;
+                break;
+            }
+        } else {
+            insert_cands(st, count, cd, pm, meta, seq_next, uint32_t(slot), D, lane);
+        }
+        seq_next += uint32_t(cd.nc);
+        PT(PH_INSERT)
     }
 
-    int slot;
-    if constexpr (DEEP) slot = S.iter;  // one slot per iteration, never reused
-    else slot = alloc_snapshot<NS, G>(S.st, D, g);
-    if (slot < 0) return true;
-    write_snapshot<G>(w, W, SW, slot, nbits, uint32_t(m[0]) | (uint32_t(m[1]) << 16),
-                      uint32_t(m[2]) | (uint32_t(m[3]) << 16), node_s, snap_lam);
-    S.cur_snap = uint32_t(slot);
-    S.applied = 0u;
-    S.beta_dirty = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) S.cm[j] = m[j];
-    S.cs = node_s;
-    S.clam = node_lam;
-    S.cur_lo = S.valid_lo = node_lam;
-    PTS(PH_SNAP)
-    S.ops += uint32_t(cd.nc) * S.stack_cost;
-    if constexpr (DEEP) {
-        S.count = mem_insert(ms, S.count, cd, pm, meta, S.seq_next, uint32_t(slot), D, lane);
-        if (S.count < 0) {  // the entry region is full (excluded by its sizing)
-            S.status = POLAR_TIMEOUT;
-            return true;
-        }
-    } else {
-        insert_cands<NS, G>(S.st, S.count, cd, pm, meta, S.seq_next, uint32_t(slot), D, g);
-    }
-    S.seq_next += uint32_t(cd.nc);
-    PTS(PH_INSERT)
-#undef PTS
-    ++S.iter;
-    return false;
-}
-
-// the decided frame's output: message words, metric, status, counters
-template <int G, int NS, bool STATS>
-__device__ __forceinline__ void search_output(Search<G, NS> &S, const Args &a, const Code &c, const Frame<G> &w,
-                                              unsigned b, uint32_t *orow) {
-    const Grp<G> g = w.g;
-    const int lane = g.lane;
-    const int W = c.W;
-    if (S.out_src == 2) {
-        const uint32_t *sp = w.scr + size_t(S.first_slot) * c.snap_words;
+    // ---- output ----
+    if (out_src == 2) {
+        const uint32_t *sp = w.scr + size_t(first_slot) * SW;
         #pragma unroll 1
-        for (int k = lane; k < W; k += G) w.beta[k] = sp[k];
-    } else if (S.out_src == 0) {
+        for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
+    } else if (out_src == 0) {
         #pragma unroll 1
-        for (int k = lane; k < W; k += G) w.beta[k] = 0u;
+        for (int k = lane; k < W; k += 32) w.beta[k] = 0u;
     }
-    g.sync();
-    if (!c.systematic) S.ops += uint32_t(c.n) * uint32_t(W);
-    write_output<G>(c, w.beta, orow, g);
+    __syncwarp();
+    if (!c.systematic) ops += uint32_t(n) * uint32_t(W);
+    write_output(c, w.beta, orow, lane);
     if (lane == 0) {
-        if (S.status == POLAR_TIMEOUT) S.out_pm = __int_as_float(0x7f800000);
-        a.pm_out[b] = S.out_pm;
-        a.status_out[b] = int8_t(S.status);
+        if (status == POLAR_TIMEOUT) out_pm = __int_as_float(0x7f800000);
+        a.pm_out[b] = out_pm;
+        a.status_out[b] = int8_t(status);
         if (STATS && a.stats_out) {  // without counters all counting is dead code
             uint32_t *sr = a.stats_out + size_t(b) * 4;
-            sr[0] = S.n_iter;
-            sr[1] = S.n_switch;
-            sr[2] = S.ops;
-            sr[3] = S.n_exp;
+            sr[0] = n_iter;
+            sr[1] = n_switch;
+            sr[2] = ops;
+            sr[3] = n_exp;
         }
-#ifdef POLAR_PHASE_TIMERS
-        for (int q = 0; q < PH_N; ++q) atomicAdd(&g_phase_cycles[q], S.pt_acc[q]);
-#endif
     }
-    g.sync();
+    __syncwarp();
+    PT(PH_OUT)
+    PT_FLUSH
 }
 
-// one frame from start to finish
-template <int G, int NS, bool EXACT, bool STATS>
-__device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Frame<G> &w,
-                                             unsigned b, uint32_t *orow, const MemStack ms) {
-    Search<G, NS> S;
-    search_init<G, NS>(S, c, D, L, w, ms);
-    while (!search_step<G, NS, EXACT, STATS>(S, c, w)) {
-    }
-    search_output<G, NS, STATS>(S, a, c, w, b, orow);
-}
-
-// resident blocks of 4 warps per SM the register budget is sized for
-template <bool MIXED, int G>
-constexpr int kMinBlocks = MIXED ? 6 : (G == 32 ? 8 : 6);
-
-// Groups of G lanes, each decoding one frame at a time, persistent: a group
-// claims `chunk` frames at a time.  MIXED = false: every frame uses a.code,
-// a.D, a.L and row b of the LLR and message buffers.  MIXED = true: frame b
-// has its own code, D and L (a.frames[b]) and offsets into packed LLR and
-// message buffers.  a.warp_smem is the shared memory of one group.
-template <bool MIXED, int G, int NS, bool EXACT, bool STATS>
-__global__ void __launch_bounds__(128, (kMinBlocks<MIXED, G>)) scs_decode_kernel(Args a) {
+// One warp per frame, persistent: warps claim `chunk` frames at a time.
+// MIXED = false: every frame uses a.code, a.D, a.L and row b of the LLR and
+// message buffers.  MIXED = true: frame b has its own code, D and L
+// (a.frames[b]) and offsets into packed LLR and message buffers.
+template <bool MIXED, int NS, bool EXACT, bool STATS>
+__global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Code codes_s[MIXED ? kMaxCodes : 1];
     if (MIXED) {
         for (int i = threadIdx.x; i < a.ncodes; i += blockDim.x) codes_s[i] = a.codes[i];
         __syncthreads();
     }
-    constexpr int F = 32 / G;  // frames a warp decodes at once
-    const int wlane = threadIdx.x & 31;
-    const int gi = wlane / G;
-    const Grp<G> g{wlane % G, gi * G, Grp<G>::GM << (gi * G)};
-    const int lane = g.lane;
+    const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int grp = wib * F + gi;  // group in the block
-    unsigned char *my = smem + size_t(grp) * a.warp_smem;
-    const int ggrp = blockIdx.x * ((blockDim.x >> 5) * F) + grp;
-    uint32_t *scr = a.scratch + size_t(ggrp) * size_t(a.scratch_stride);
+    unsigned char *my = smem + size_t(wib) * a.warp_smem;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
+    uint32_t *scr = a.scratch + size_t(gwarp) * size_t(a.scratch_stride);
     for (;;) {
         unsigned b0 = 0;
         if (lane == 0) b0 = atomicAdd(a.counter, unsigned(a.chunk));
-        b0 = g.shfl(b0, 0);
+        b0 = __shfl_sync(FULL, b0, 0);
         if (b0 >= unsigned(a.B)) break;
         const unsigned b1 = min(unsigned(a.B), b0 + unsigned(a.chunk));
         for (unsigned k = b0; k < b1; ++k) {
@@ -1591,13 +1371,13 @@ __global__ void __launch_bounds__(128, (kMinBlocks<MIXED, G>)) scs_decode_kernel
             if (MIXED && b >= unsigned(a.B)) continue;
             if constexpr (!MIXED) {
                 const Code &c = a.code;
-                Frame<G> w{g, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
-                           my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
+                Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
+                       my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
                 MemStack ms{nullptr, nullptr, 0};
                 if constexpr (NS == 0)
                     ms = MemStack{reinterpret_cast<uint4 *>(scr + a.deep_ent_off),
                                   reinterpret_cast<uint2 *>(my + a.deep_best_off), a.deep_cap};
-                decode_frame<G, NS, EXACT, STATS>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words, ms);
+                decode_frame<NS, EXACT, STATS>(a, c, a.D, a.L, w, b, a.info_out + size_t(b) * c.info_words, ms);
             } else {
                 const int4 fd = a.frames[b];
                 if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
@@ -1609,369 +1389,11 @@ __global__ void __launch_bounds__(128, (kMinBlocks<MIXED, G>)) scs_decode_kernel
                 }
                 const Code &c = codes_s[fd.x];
                 const long long lo = a.llr_off[b];
-                Frame<G> w{g, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
-                           reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo,
-                           c.scales};
-                decode_frame<G, NS, false, STATS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b],
-                                                  MemStack{nullptr, nullptr, 0});
+                Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
+                       reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales};
+                decode_frame<NS, false, STATS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b], MemStack{nullptr, nullptr, 0});
             }
         }
-    }
-}
-
-// Lane groups in lock step (G = 8 or 16, one code for the whole batch).  The
-// warp runs one uniform program: every trip of its loop is one search
-// iteration (Sec. 2.2.5) of each group that holds a frame, in phases -- pop,
-// restore, the schedule walk as a loop of micro-ops that runs until every
-// group has reached its branching node, node decoding, snapshot and insert
-// -- with the whole warp reconverging after each phase, so that groups at
-// different positions of their searches still share the phases'
-// instructions.  A group whose frame is decided writes it out and claims the
-// next frame at the end of the trip.  The arithmetic of each frame is that
-// of search_step, operation for operation.
-// resident blocks of 4 warps per SM of the lock-step kernel: shared memory
-// (32 / G frames a warp) allows about 3 for G = 8 and 6 for G = 16
-template <int G>
-constexpr int kLockstepBlocks = G == 8 ? 3 : 5;
-
-template <int G, int NS, bool STATS>
-__global__ void __launch_bounds__(128, kLockstepBlocks<G>) scs_decode_lockstep_kernel(Args a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int F = 32 / G;  // frames a warp decodes at once
-    const int wlane = threadIdx.x & 31;
-    const int gi = wlane / G;
-    const Grp<G> g{wlane % G, gi * G, Grp<G>::GM << (gi * G)};
-    const int lane = g.lane;
-    const int wib = threadIdx.x >> 5;
-    const int grp = wib * F + gi;  // group in the block
-    unsigned char *my = smem + size_t(grp) * a.warp_smem;
-    const int ggrp = blockIdx.x * ((blockDim.x >> 5) * F) + grp;
-    uint32_t *scr = a.scratch + size_t(ggrp) * size_t(a.scratch_stride);
-    const Code &c = a.code;
-    const int N = c.N, W = c.W, n = c.n, SW = c.snap_words;
-    const int D = a.D, L = a.L;
-    float *alpha = reinterpret_cast<float *>(my);
-    uint32_t *beta = reinterpret_cast<uint32_t *>(my + 4 * N);
-    uint8_t *cnt = my + 4 * N + 4 * W;
-    const MemStack none{nullptr, nullptr, 0};
-    const uint4 *opsv = reinterpret_cast<const uint4 *>(c.ops);
-    Search<G, NS> S;
-    unsigned b = 0;
-    if (lane == 0) b = atomicAdd(a.counter, 1u);
-    b = g.shfl(b, 0);
-    bool active = b < unsigned(a.B);
-    if (active) {
-        const Frame<G> w{g, n, a.llr_vec, alpha, beta, cnt, scr, a.llr + size_t(b) * N, c.scales};
-        search_init<G, NS>(S, c, D, L, w, none);
-    }
-    for (;;) {
-        if (!__any_sync(FULL, active)) break;
-        const Frame<G> w{g, n, a.llr_vec, alpha, beta, cnt, scr, a.llr + size_t(b) * N, c.scales};
-        bool live = active && S.iter < S.max_iter;  // takes a search iteration in this trip
-        bool fin = active && !live;                  // decided (the guard: status stays TIMEOUT)
-        if (live && S.count == 0) {                  // every path deleted (reading R12)
-            S.status = POLAR_CRC_FAIL;
-            if (S.have_first) {
-                S.out_pm = S.first_pm;
-                S.out_src = 2;
-            }
-            live = false;
-            fin = true;
-        }
-        // ---- pop the best path: smallest pm, ties to the newest ----
-        uint32_t p_pmb = 0u, p_meta = 0u, p_aux = 0u;
-        if (live) {
-            uint32_t lp = S.st.pm[0], ls = S.st.seq[0];
-            int lj = 0;
-#pragma unroll
-            for (int j = 1; j < NS; ++j)
-                if (S.st.pm[j] < lp || (S.st.pm[j] == lp && S.st.pm[j] != EMPTY && S.st.seq[j] > ls)) {
-                    lp = S.st.pm[j];
-                    ls = S.st.seq[j];
-                    lj = j;
-                }
-            const uint32_t gp = g.rmin(lp);
-            const uint32_t gs = g.rmax(lp == gp ? ls : 0u);
-            const uint32_t bal = g.ballot(lp == gp && ls == gs);
-            const int wl = __ffs(bal) - 1;
-            p_pmb = gp;
-            uint32_t my_meta = S.st.meta[0], my_aux = S.st.aux[0];  // this lane's best entry
-#pragma unroll
-            for (int j = 1; j < NS; ++j)
-                if (lj == j) {
-                    my_meta = S.st.meta[j];
-                    my_aux = S.st.aux[j];
-                }
-            p_meta = g.shfl(my_meta, wl);
-            p_aux = g.shfl(my_aux, wl);
-            if (gp == EMPTY) {  // count out of step with the slots: stop safely
-                S.status = POLAR_TIMEOUT;
-                live = false;
-                fin = true;
-            } else if (lane == wl) {
-#pragma unroll
-                for (int j = 0; j < NS; ++j)
-                    if (lj == j) S.st.pm[j] = EMPTY;
-            }
-        }
-        const int p_sched = int(p_meta >> 16);
-        const uint32_t p_snap = p_aux & NOSNAP;
-        const uint32_t p_mask = (p_aux >> 8) & 0x1Fu;
-        if (live) {
-            --S.count;
-            ++S.n_iter;
-            S.ops += S.stack_cost;
-            if ((p_snap != NOSNAP && p_snap >= uint32_t(S.first_slot)) || p_sched > c.nops) {
-                S.status = POLAR_TIMEOUT;  // never produced; guards the scratch and schedule indices
-                live = false;
-                fin = true;
-            }
-        }
-        __syncwarp();
-
-        // ---- restore the path's beta array ----
-        bool switched = false;
-        int div = 0;  // first bit where the popped path's beta differs from the working one
-        if (live) {
-            if (p_snap == S.cur_snap) {
-                if (S.beta_dirty) {
-                    const uint32_t *sp = scr + size_t(S.cur_snap) * SW;
-                    #pragma unroll 1
-                    for (int k = lane; k < W; k += G) beta[k] = sp[k];
-                    g.sync();
-                    S.applied = 0u;
-                    S.beta_dirty = false;
-                    S.valid_lo = S.cur_lo;
-                }
-                w.apply_flips(S.applied ^ p_mask, S.cm, S.cs, S.clam);
-                S.applied = p_mask;
-            } else {  // path switch (Sec. 3.3)
-                switched = true;
-                ++S.n_switch;
-                S.ops += uint32_t(W);
-                div = restore_switch<G>(scr + size_t(p_snap) * SW, beta, W, p_mask, g);
-                S.beta_dirty = true;
-            }
-            if (p_sched == c.nops) {  // a complete path
-                if (switched) S.valid_lo = n;  // beta replaced, alpha left as it was
-                bool pass = true;
-                if (c.crc) {
-                    S.ops += uint32_t(c.crc) * uint32_t(W);
-                    pass = crc_ok<G>(c, beta, g);
-                }
-                if (pass) {
-                    S.status = POLAR_OK;
-                    S.out_pm = __uint_as_float(p_pmb);
-                    S.out_src = 1;
-                    fin = true;
-                } else {
-                    ++S.crc_fails;
-                    if (!S.have_first) {
-                        S.have_first = true;
-                        S.first_pm = __uint_as_float(p_pmb);
-                        uint32_t *sp = scr + size_t(S.first_slot) * SW;
-                        #pragma unroll 1
-                        for (int k = lane; k < W; k += G) sp[k] = beta[k];
-                        g.sync();
-                    }
-                    if (S.crc_fails >= L) {
-                        S.status = POLAR_CRC_FAIL;
-                        S.out_pm = S.first_pm;
-                        S.out_src = 2;
-                        fin = true;
-                    } else {
-                        ++S.iter;
-                    }
-                }
-                live = false;
-            }
-        }
-
-        // ---- alpha after a switch (Alg. calp), as in search_step ----
-        int rl = -1, lam_d = 0, s_d = 0;
-        if (live && switched) {
-            const uint32_t tgt = __ldg(&c.ops[p_sched].z);
-            if (tgt != NO_TARGET) {
-                lam_d = int(tgt & 0xFFu);
-                s_d = int(tgt >> 8);
-                S.ops += 2u * uint32_t(N - (1 << lam_d));  // counted as the full recompute
-                int lam = n - 1;
-                while (lam >= lam_d && lam >= S.valid_lo && (s_d >> lam) == (S.cs >> lam) &&
-                       div >= ((s_d >> lam) << lam))
-                    --lam;
-                rl = lam;
-            }
-        }
-        __syncwarp();
-
-        // ---- the schedule walk to the next branching node (Sec. 4), one
-        // micro-op of every walking group per trip of this loop ----
-        float pm = __uint_as_float(p_pmb);
-        int t = p_sched;
-        uint4 nxt = make_uint4(0u, 0u, 0u, 0u), op = nxt;
-        if (live) {
-            nxt = __ldg(opsv + min(t, c.nops - 1));
-            op = nxt;
-        }
-        bool walking = live;
-        for (;;) {
-            uint32_t code = OP_F;
-            int lam = 0, s = 0, run = 1;
-            bool sched = true;
-            if (walking) {
-                sched = rl < lam_d;  // else: a recomputed spine stage
-                if (!sched) {
-                    lam = rl;
-                    s = (s_d >> lam) << lam;
-                    code = ((s_d >> lam) & 1) ? OP_G : OP_F;
-                    --rl;
-                } else if (t >= c.nops) {
-                    walking = false;
-                } else {
-                    op = nxt;
-                    if (t + 1 < c.nops) nxt = __ldg(opsv + t + 1);
-                    code = op.x & 0xFFu;
-                    lam = int((op.x >> 8) & 0xFFu);
-                    s = int(op.y);
-                    run = int((op.x >> 16) & 0xFFu) + 1;
-                    if (code >= OP_BRANCH) walking = false;
-                    else ++t;
-                }
-            }
-            if (!__any_sync(FULL, walking)) break;
-            if (walking) {
-                if (code <= OP_G) {  // an F or G, then run - 1 F ops down the left edge
-                    #pragma unroll 1
-                    for (int i = 0; i < run; ++i) {
-                        w.op_fg(lam - i, s, i == 0 && code == OP_G);
-                        if (sched) S.ops += 2u << (lam - i);
-                    }
-                } else if (code == OP_COMB) {  // run combines, one stage up each
-                    #pragma unroll 1
-                    for (int i = 0; i < run; ++i) {
-                        w.op_comb(lam + i, s);
-                        S.ops += (lam + i < 5) ? 1u : (1u << (lam + i - 5));
-                        s -= 1 << (lam + i);
-                    }
-                } else {  // Rate-0 node or frozen leaf: beta = 0, PM += sum HD(a)|a|
-                    const float pen = w.node_sum(lam, 1);
-                    w.set_range(lam, s, 0u);
-                    pm = __fadd_rn(pm, pen);
-                    S.ops += (2u << lam) + 1u;
-                }
-            }
-            __syncwarp();
-        }
-
-        // ---- the expansion's candidates ----
-        Cands cd{0, 0u, false, 0.0f, 0.0f, {0.0f, 0.0f, 0.0f, 0.0f}};
-        int m[4] = {0, 0, 0, 0};
-        int node_s = 0, node_lam = n, snap_lam = 0, nbits = N;
-        uint32_t meta = uint32_t(N) | (uint32_t(c.nops) << 16);
-        if (live) {
-            ++S.n_exp;
-            if (t >= c.nops) {
-                cd.nc = 1;
-                S.ops += 1u;
-            } else {
-                const uint32_t code = op.x & 0xFFu;
-                const int lam = int((op.x >> 8) & 0xFFu);
-                const int s = int(op.y);
-                const int len = 1 << lam;
-                node_s = s;
-                node_lam = snap_lam = lam;
-                nbits = s + len;
-                meta = uint32_t(s + len) | (uint32_t(t + 1) << 16);
-                uint32_t vc = 0;
-                if (lane == 0) vc = ++cnt[op.w];
-                vc = g.shfl(vc, 0);
-                g.sync();
-                if (int(vc) >= L) {  // the L-prune (Sec. 2.2.5)
-                    S.ops += S.stack_cost;
-                    int removed = 0;
-#pragma unroll
-                    for (int j = 0; j < NS; ++j) {
-                        const bool kill = S.st.pm[j] != EMPTY && int(S.st.meta[j] & 0xFFFFu) <= s;
-                        removed += __popc(g.ballot(kill));
-                        if (kill) S.st.pm[j] = EMPTY;
-                    }
-                    S.count -= removed;
-                }
-                if (code == OP_REP) {
-                    float Sv, p0;
-                    uint32_t bbit;
-                    if (len <= 4 * G) {
-                        float pz, po;
-                        w.rep_sums(lam, Sv, pz, po);
-                        bbit = Sv < 0.0f ? 1u : 0u;
-                        p0 = bbit ? po : pz;
-                    } else {
-                        Sv = w.node_sum(lam, 0);
-                        bbit = Sv < 0.0f ? 1u : 0u;
-                        p0 = w.node_sum(lam, bbit ? 2 : 1);
-                    }
-                    w.set_range(lam, s, bbit);
-                    cd.nc = 2;
-                    cd.rep = true;
-                    cd.rep0 = p0;
-                    cd.rep1 = __fadd_rn(p0, fabsf(Sv));
-                    S.ops += 4u * uint32_t(len) + 3u;
-                } else {  // information leaf, Rate-1 or SPC: hard decisions first
-                    const uint32_t q = w.node_hd(lam, s);
-                    if (code == OP_LEAF1) {
-                        cd.mag[0] = fabsf(w.stage(0)[0]);
-                        cd.nc = 2;
-                        cd.masks = LEAF1_MASKS;
-                        S.ops += 4u;
-                    } else {
-                        const bool spc = code == OP_SPC;
-                        w.node_least(lam, spc ? 4 : 2, m, cd.mag);
-                        cd.nc = spc ? 8 : 4;
-                        cd.masks = spc ? (q ? SPC_MASKS_ODD : SPC_MASKS_EVEN) : R1_MASKS;
-                        S.ops += spc ? 10u * uint32_t(len) + (q ? 16u : 17u) : 6u * uint32_t(len) + 5u;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-
-        // ---- snapshot and insert ----
-        if (live) {
-            const int slot = alloc_snapshot<NS, G>(S.st, D, g);
-            if (slot < 0) {  // cannot happen (the extended path left the stack)
-                live = false;
-                fin = true;
-            } else {
-                write_snapshot<G>(w, W, SW, slot, nbits, uint32_t(m[0]) | (uint32_t(m[1]) << 16),
-                                  uint32_t(m[2]) | (uint32_t(m[3]) << 16), node_s, snap_lam);
-                S.cur_snap = uint32_t(slot);
-                S.applied = 0u;
-                S.beta_dirty = false;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) S.cm[j] = m[j];
-                S.cs = node_s;
-                S.clam = node_lam;
-                S.cur_lo = S.valid_lo = node_lam;
-                S.ops += uint32_t(cd.nc) * S.stack_cost;
-                insert_cands<NS, G>(S.st, S.count, cd, pm, meta, S.seq_next, uint32_t(slot), D, g);
-                S.seq_next += uint32_t(cd.nc);
-                ++S.iter;
-            }
-        }
-        __syncwarp();
-
-        // ---- decided frames: output, then the group's next frame ----
-        if (fin) {
-            search_output<G, NS, STATS>(S, a, c, w, b, a.info_out + size_t(b) * c.info_words);
-            if (lane == 0) b = atomicAdd(a.counter, 1u);
-            b = g.shfl(b, 0);
-            active = b < unsigned(a.B);
-            if (active) {
-                const Frame<G> w2{g, n, a.llr_vec, alpha, beta, cnt, scr, a.llr + size_t(b) * N, c.scales};
-                search_init<G, NS>(S, c, D, L, w2, none);
-            }
-        }
-        __syncwarp();
     }
 }
 
@@ -1998,7 +1420,6 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
     for (int i = threadIdx.x; i < a.ncodes; i += blockDim.x) codes_s[i] = a.codes[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const Grp<32> g{lane, 0, FULL};
     const int wib = threadIdx.x >> 5;
     unsigned char *my = smem + size_t(wib) * a.warp_smem;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -2039,10 +1460,9 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
             #pragma unroll 1
             for (int i = lane; i < c.N; i += 32) stage[i] = __ldcg(src + i);
             __syncwarp();
-            Frame<32> w{g, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
-                        my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
-            decode_frame<32, NS, false, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k],
-                                               MemStack{nullptr, nullptr, 0});
+            Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
+                   my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
+            decode_frame<NS, false, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k], MemStack{nullptr, nullptr, 0});
         }
         if (lane == 0) {
             a.t_done[k] = global_ns();
@@ -2079,61 +1499,31 @@ Code make_code(const polar_plan *p, const KOp *ops, const uint32_t *crc_rows, co
 
 int warp_smem_bytes(int N, int W, int nbranch) { return ((4 * N + 4 * W + nbranch) + 15) & ~15; }
 
-// The instantiation of the decoder for one launch: mixed or uniform, G lanes
-// per frame, stack slots per lane, exact-f or min-sum, with or without
-// counters.
-template <bool MIXED, int G, int NS, bool EXACT, bool STATS>
+// The instantiation of the decoder for one launch: mixed or uniform, one or
+// two stack rows per lane, exact-f or min-sum, with or without counters.
+template <bool MIXED, int NS, bool EXACT, bool STATS>
 const void *kernel_fn() {
-    return reinterpret_cast<const void *>(scs_decode_kernel<MIXED, G, NS, EXACT, STATS>);
+    return reinterpret_cast<const void *>(scs_decode_kernel<MIXED, NS, EXACT, STATS>);
 }
 
-// a register stack of D <= 64 entries on groups of G lanes: 32 / G slots a
-// lane for D <= 32, twice that up to 64
-template <int G, int NS, bool STATS>
-const void *lockstep_fn() {
-    return reinterpret_cast<const void *>(scs_decode_lockstep_kernel<G, NS, STATS>);
-}
-
-template <int G>
-const void *uniform_group_kernel(int D, bool stats) {
-    constexpr int NS1 = 32 / G;
-    if constexpr (G == 32) {
-        if (D > 32) return stats ? kernel_fn<false, 32, 2, false, true>() : kernel_fn<false, 32, 2, false, false>();
-        return stats ? kernel_fn<false, 32, 1, false, true>() : kernel_fn<false, 32, 1, false, false>();
-    } else {
-        if (D > 32) return stats ? lockstep_fn<G, 2 * NS1, true>() : lockstep_fn<G, 2 * NS1, false>();
-        return stats ? lockstep_fn<G, NS1, true>() : lockstep_fn<G, NS1, false>();
-    }
-}
-
-// lanes per frame of a uniform launch: the plan's setting, else the measured
-// choice; the memory stack and exact-f decoding run on whole warps
-int frame_lanes(const polar_plan *p, int D) {
-    if (D > POLAR_MAX_D_GPU || p->exact) return 32;
-    if (p->lanes == 8 || p->lanes == 16 || p->lanes == 32) return p->lanes;
-    return 32;
-}
-
-const void *uniform_kernel(const polar_plan *p, int D, bool stats, int G) {
-    if (D > POLAR_MAX_D_GPU)
-        return stats ? kernel_fn<false, 32, 0, false, true>() : kernel_fn<false, 32, 0, false, false>();
+const void *uniform_kernel(const polar_plan *p, int D, bool stats) {
+    if (D > POLAR_MAX_D_GPU) return stats ? kernel_fn<false, 0, false, true>() : kernel_fn<false, 0, false, false>();
+    const bool two = D > 32;
     if (p->exact) {
-        if (D > 32) return stats ? kernel_fn<false, 32, 2, true, true>() : kernel_fn<false, 32, 2, true, false>();
-        return stats ? kernel_fn<false, 32, 1, true, true>() : kernel_fn<false, 32, 1, true, false>();
+        if (two) return stats ? kernel_fn<false, 2, true, true>() : kernel_fn<false, 2, true, false>();
+        return stats ? kernel_fn<false, 1, true, true>() : kernel_fn<false, 1, true, false>();
     }
-    if (G == 8) return uniform_group_kernel<8>(D, stats);
-    if (G == 16) return uniform_group_kernel<16>(D, stats);
-    return uniform_group_kernel<32>(D, stats);
+    if (two) return stats ? kernel_fn<false, 2, false, true>() : kernel_fn<false, 2, false, false>();
+    return stats ? kernel_fn<false, 1, false, true>() : kernel_fn<false, 1, false, false>();
 }
 
 const void *mixed_kernel(int Dmax, bool stats) {
-    if (Dmax > 32) return stats ? kernel_fn<true, 32, 2, false, true>() : kernel_fn<true, 32, 2, false, false>();
-    return stats ? kernel_fn<true, 32, 1, false, true>() : kernel_fn<true, 32, 1, false, false>();
+    if (Dmax > 32) return stats ? kernel_fn<true, 2, false, true>() : kernel_fn<true, 2, false, false>();
+    return stats ? kernel_fn<true, 1, false, true>() : kernel_fn<true, 1, false, false>();
 }
 
-// block size and persistent grid for kernel `fn` with `frame_smem` bytes per
-// frame and `fpw` frames decoded at once by a warp (32 / G)
-int launch_shape(const void *fn, bool mixed, int frame_smem, int fpw, int B, int wpb, int *grid_out, int *wpb_out,
+// block size and persistent grid for kernel `fn` with `warp_smem` bytes per warp
+int launch_shape(const void *fn, bool mixed, int warp_smem, int B, int wpb, int *grid_out, int *wpb_out,
                  int *smem_out) {
     int dev = 0, sms = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -2142,7 +1532,6 @@ int launch_shape(const void *fn, bool mixed, int frame_smem, int fpw, int B, int
     if (e != cudaSuccess) return cuda_status(e);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int static_smem = mixed ? int(sizeof(Code)) * kMaxCodes : int(sizeof(Code));
-    const int warp_smem = fpw * frame_smem;
     while (wpb > 1 && wpb * warp_smem + static_smem > max_smem) wpb >>= 1;
     if (wpb * warp_smem + static_smem > max_smem) return POLAR_ELIMIT;
     const int smem = wpb * warp_smem;
@@ -2153,8 +1542,7 @@ int launch_shape(const void *fn, bool mixed, int frame_smem, int fpw, int B, int
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return POLAR_ELIMIT;
     long long grid = (long long)sms * per_sm;
-    const long long per_block = (long long)wpb * fpw;
-    const long long want = ((long long)B + per_block - 1) / per_block;
+    const long long want = (long long)(B + wpb - 1) / wpb;
     if (want < grid) grid = want;
     *grid_out = int(grid);
     *wpb_out = wpb;
@@ -2185,8 +1573,6 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
     a.chunk = 1;
     a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
-    const int G = frame_lanes(p, D);
-    const int fpw = 32 / G;
     int wpb_pref = 4;
     long long deep_fit = 0;
     if (D > POLAR_MAX_D_GPU) {  // the memory stack
@@ -2206,15 +1592,14 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
     }
 
     int grid = 0, wpb = 0, smem = 0;
-    const void *fn = uniform_kernel(p, D, d_stats != nullptr, G);
-    int rc = launch_shape(fn, false, a.warp_smem, fpw, B, wpb_pref, &grid, &wpb, &smem);
+    const void *fn = uniform_kernel(p, D, d_stats != nullptr);
+    int rc = launch_shape(fn, false, a.warp_smem, B, wpb_pref, &grid, &wpb, &smem);
     if (rc) return rc;
     if (deep_fit > 0 && (long long)grid * wpb > deep_fit) grid = int(deep_fit / wpb);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
-    const size_t groups = size_t(grid) * size_t(wpb) * size_t(fpw);
-    const size_t bytes = 64 + groups * size_t(a.scratch_stride) * 4;
+    const size_t bytes = 64 + size_t(grid) * size_t(wpb) * size_t(a.scratch_stride) * 4;
     void *ws = nullptr;
     keep_pool_memory(dev);
     e = cudaMallocAsync(&ws, bytes, stream);
@@ -2317,7 +1702,7 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     int grid = 0, wpb = 0, smem = 0;
     const int nb_units = (B + chunk - 1) / chunk;
     const void *fn = mixed_kernel(Dmax, d_stats != nullptr);
-    int rc = launch_shape(fn, true, a.warp_smem, 1, nb_units, wpb_pref, &grid, &wpb, &smem);
+    int rc = launch_shape(fn, true, a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem);
     if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -2526,21 +1911,18 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     a.chunk = 1;
     a.scratch_stride = (long long)(D + 1) * a.code.snap_words;
 
-    // as many resident frame groups as the static scratch holds (the kernel is
-    // persistent and claims frames dynamically, so fewer groups only cost speed)
-    const size_t per_group = size_t(a.scratch_stride) * 4;
-    const size_t groups_fit = (kStaticScratchBytes - 64) / per_group;
-    if (groups_fit < 1) return POLAR_ESCRATCH;
-    int G = frame_lanes(p, D);
-    while (G < 32 && groups_fit < size_t(32 / G)) G *= 2;
-    const int fpw = 32 / G;
+    // as many resident warps as the static scratch holds (the kernel is
+    // persistent and claims frames dynamically, so fewer warps only cost speed)
+    const size_t per_warp = size_t(a.scratch_stride) * 4;
+    const size_t warps_fit = (kStaticScratchBytes - 64) / per_warp;
+    if (warps_fit < 1) return POLAR_ESCRATCH;
     int wpb = 4;
-    while (wpb > 1 && size_t(wpb) * size_t(fpw) > groups_fit) wpb >>= 1;
+    while (wpb > 1 && size_t(wpb) > warps_fit) wpb >>= 1;
     int grid = 0, smem = 0;
-    const void *fn = uniform_kernel(p, D, d_stats != nullptr, G);
-    rc = launch_shape(fn, false, a.warp_smem, fpw, B, wpb, &grid, &wpb, &smem);
+    const void *fn = uniform_kernel(p, D, d_stats != nullptr);
+    rc = launch_shape(fn, false, a.warp_smem, B, wpb, &grid, &wpb, &smem);
     if (rc) return rc;
-    const long long fit = (long long)(groups_fit / (size_t(wpb) * size_t(fpw)));
+    const long long fit = (long long)(warps_fit / size_t(wpb));
     if (fit < grid) grid = int(fit);
 
     a.counter = static_cast<unsigned *>(areas.scratch);

@@ -164,13 +164,3 @@ def test_set_exact_host_checks(lib):
     with pytest.raises(ps.PolarError) as e:
         ps.PlanSet([ex])
     assert e.value.rc == ps.POLAR_EINVAL
-
-
-def test_set_lanes_host_checks(lib):
-    """polar_plan_set_lanes takes 0 (automatic), 8, 16 or 32 lanes per frame."""
-    plan = ps.Plan(64, 32, ps.polar_construct(64, 32, 0.0))
-    for bad in (1, 4, 12, 64, -8):
-        assert lib.polar_plan_set_lanes(plan.handle, bad) == ps.POLAR_EINVAL
-    for ok in (0, 8, 16, 32):
-        assert lib.polar_plan_set_lanes(plan.handle, ok) == 0
-    assert lib.polar_plan_set_lanes(None, 8) == ps.POLAR_EINVAL
