@@ -1084,7 +1084,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
                 beta_dirty = false;
                 valid_lo = cur_lo;
             }
-            w.apply_flips(applied ^ p_mask, cm, cs, clam);
+            if (applied ^ p_mask) w.apply_flips(applied ^ p_mask, cm, cs, clam);
             applied = p_mask;
         } else {  // path switch (Sec. 3.3)
             switched = true;
@@ -1139,10 +1139,13 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
                 lam_d = int(tgt & 0xFFu);
                 s_d = int(tgt >> 8);
                 ops += 2u * uint32_t(N - (1 << lam_d));  // counted as the full recompute
-                int lam = n - 1;
-                while (lam >= lam_d && lam >= valid_lo && (s_d >> lam) == (cs >> lam) && div >= ((s_d >> lam) << lam))
-                    --lam;
-                rl = lam;
+                // each condition of the reuse test holds on a range lam >= T_k,
+                // so the first stage to recompute is one below their maximum
+                const uint32_t xs = uint32_t(s_d ^ cs);
+                int T = max(lam_d, valid_lo);
+                if (xs) T = max(T, 32 - __clz(xs));
+                if (div < s_d) T = max(T, 32 - __clz(uint32_t(s_d ^ div)));
+                rl = min(n - 1, T - 1);
             }
         }
         PT(PH_ALPHA)
