@@ -396,6 +396,13 @@ def bench_ours(args, rank: int, world: int, local_rank: int, base=WORKLOAD) -> N
     e2e = None
     if not args.no_e2e:
         e2e = bench_e2e(ps, plan, llrs, w, args, world)
+    mixed = None
+    if base is WORKLOAD and world == 1 and not args.no_mixed:
+        # the batching claim (config 3 of the workload) beside the sweep: the
+        # batched path against per-configuration launches on the same frames
+        del llrs, outs
+        torch.cuda.empty_cache()
+        mixed = measure_mixed(args, MIXED["frames"], rank, local_rank, steps=3, warmup=1, with_roofline=False)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_frames, w)
@@ -420,6 +427,8 @@ def bench_ours(args, rank: int, world: int, local_rank: int, base=WORKLOAD) -> N
                 "config": config,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": npts * args.steps,
                 "clocks": clocks}
+        if mixed is not None:
+            line["mixed"] = mixed
         print(json.dumps(line), flush=True)
 
 
@@ -542,18 +551,17 @@ def make_mixed_inputs(ps, frames: int, rank: int, w=MIXED):
                 words=words, msg=msg_flat, Ns=Ns, Ks=Ks)
 
 
-def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
-    """One persistent launch over the whole mixed batch (tuned, replayed from a
-    CUDA graph) against one launch per (code, D) configuration, on the same
-    frames; both must give identical outputs."""
+def measure_mixed(args, B: int, rank: int, local_rank: int, steps: int, warmup: int, with_roofline: bool) -> dict:
+    """The mixed batch (config 3 of the workload) three ways on the same
+    frames: split by stack rows into two persistent launches on two streams
+    (scs_decode_mixed_split, tuned, replayed from one captured CUDA graph),
+    one persistent launch (scs_decode_mixed, graph-replayed), and one launch
+    per (code, D) configuration; all three must give identical outputs."""
     import numpy as np
     import torch
 
     import paper_1809_03606_gb300 as ps
 
-    torch.cuda.set_device(local_rank)
-    ps.load(build_if_missing=True)
-    B = int(args.frames) if args.frames else MIXED["frames"]
     m = make_mixed_inputs(ps, B, rank)
     pset = ps.PlanSet(m["plans"])
     fr = np.zeros((B, 4), np.int32)
@@ -568,24 +576,32 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
     pm = torch.empty(B, dtype=torch.float32, device="cuda")
     st = torch.empty(B, dtype=torch.int8, device="cuda")
     order = torch.from_numpy(ps.polar_mixed_order(pset, fr)).cuda() if not args.no_lpt else None  # longest first
+    sorder_np, n_two = ps.polar_mixed_split_order(pset, fr)
+    sorder = torch.from_numpy(sorder_np).cuda()
     margs = (pset, frames, Dmax, m["llr"], llr_off, info, info_off, pm, st)
     ps.scs_decode_mixed(*margs, order=order)
     torch.cuda.synchronize()
     nsample = min(B, 200_000)
     sfr = fr[:nsample]
-    sorder = torch.from_numpy(ps.polar_mixed_order(pset, sfr)).cuda() if not args.no_lpt else None
+    tune_order = torch.from_numpy(ps.polar_mixed_order(pset, sfr)).cuda() if not args.no_lpt else None
     sample = (pset, frames[:nsample], Dmax, m["llr"], llr_off[:nsample], info, info_off[:nsample], pm[:nsample],
               st[:nsample])
-    wpb, chunk = ps.scs_tune_mixed(*sample, order=sorder)
+    wpb, chunk = ps.scs_tune_mixed(*sample, order=tune_order)
+    # first calls on a side stream (set tables, split streams), then capture
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
         ps.scs_decode_mixed(*margs, stream=stream, order=order)
+        ps.scs_decode_mixed_split(pset, frames, sorder, n_two, Dmax, m["llr"], llr_off, info, info_off, pm, st,
+                                  stream=stream)
     torch.cuda.current_stream().wait_stream(stream)
     torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
+    graph_one = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_one):
         ps.scs_decode_mixed(*margs, order=order)
+    graph_split = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_split):
+        ps.scs_decode_mixed_split(pset, frames, sorder, n_two, Dmax, m["llr"], llr_off, info, info_off, pm, st)
 
     # per-configuration launches: frames grouped by (code, D), each group's
     # LLR rows gathered into its own contiguous buffer (outside the timing)
@@ -606,23 +622,25 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
         for plan, d, x, bs_t, i_, p_, s_ in per:
             ps.scs_decode_batch(plan, x, d, d, i_, p_, s_)
 
-    def timed(fn, steps):
-        for _ in range(args.warmup):
+    def timed(fn, n):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(steps):
+        for _ in range(n):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        return e0.elapsed_time(e1) / n
 
     sampler = ClockSampler(local_rank) if rank == 0 else None
     if sampler:
         sampler.__enter__()
-    ms_mixed = timed(graph.replay, args.steps)
-    ms_per = timed(run_per_config, args.steps)
+    ms_one = timed(graph_one.replay, steps)
+    pm_one, st_one, info_one = pm.clone(), st.clone(), info.clone()
+    ms_split = timed(graph_split.replay, steps)
+    ms_per = timed(run_per_config, steps)
     if sampler:
         sampler.__exit__(None, None, None)
     # identical outputs: per-configuration results scattered back in frame order
@@ -631,47 +649,74 @@ def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
     for plan, d, x, bs_t, i_, p_, s_ in per:
         pm_per[bs_t] = p_
         st_per[bs_t] = s_
-    same = bool(torch.equal(pm_per.view(torch.int32), pm.view(torch.int32)) and torch.equal(st_per, st))
-    # roofline of the mixed launch: counted operations (one untimed launch
-    # with counters) and algorithmic bytes against the same peaks as the sweep
-    stats = torch.empty((B, 4), dtype=torch.int32, device="cuda")
-    ps.scs_decode_mixed(*margs, stats=stats, order=order)
-    torch.cuda.synchronize()
-    ops_step = float((stats[:, 2].to(torch.int64) & 0xFFFFFFFF).sum().item())
-    del stats
-    bytes_step = float(sum(4 * int(n) for n in m["Ns"]) + 4 * int(m["words"].sum()) + 5 * B)
-    peaks = measured_peaks()
-    sms = ps.polar_device_info()["sm_count"]
-    alu_peak = sms * ALU_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6
-    t_alu, t_hbm = ops_step / alu_peak, bytes_step / (peaks["hbm_gbs"] * 1e9)
-    if t_alu >= t_hbm:
-        roof = {"bound": "alu", "achieved": ops_step / (ms_mixed / 1e3) / 1e12, "peak": alu_peak / 1e12, "unit": "Top/s"}
-    else:
-        roof = {"bound": "hbm", "achieved": bytes_step / (ms_mixed / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    cpu = mixed_cpu_baseline(args.cpu_frames * 4) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    same = bool(torch.equal(pm_per.view(torch.int32), pm.view(torch.int32)) and torch.equal(st_per, st) and
+                torch.equal(pm_one.view(torch.int32), pm.view(torch.int32)) and torch.equal(st_one, st) and
+                torch.equal(info_one, info))
     kmsg = torch.from_numpy((m["Ks"] - MIXED["crc"]).astype(np.int64)).sum().item()
-    err = 0
-    info_np = info.cpu().numpy()
-    msg_np = m["msg"].cpu().numpy()
-    for b in range(0, B, max(1, B // 20000)):
-        lo = int(m["info_off"][b])
-        err += int(not np.array_equal(info_np[lo:lo + m["words"][b]], msg_np[lo:lo + m["words"][b]]))
-    fer = err / len(range(0, B, max(1, B // 20000)))
+    out = {"frames": B, "codes": len(m["keys"]), "two_row_frames": int(n_two),
+           "batched_ms": ms_split, "batched": "two persistent launches split by stack rows, two streams, one graph",
+           "single_launch_ms": ms_one, "per_config_ms": ms_per, "per_config_launches": len(per),
+           "ratio": ms_per / ms_split, "ratio_single_launch": ms_per / ms_one, "outputs_identical": same,
+           "gbps": kmsg / (ms_split / 1e3) / 1e9, "per_config_gbps": kmsg / (ms_per / 1e3) / 1e9,
+           "tuned": {"warps_per_block": wpb, "frames_per_claim": chunk},
+           "crc_fail_rate": float((st != 0).double().mean().item()),
+           "clocks": sampler.summary() if sampler else None}
+    if with_roofline:
+        # counted operations (one untimed launch with counters) and algorithmic
+        # bytes against the same peaks as the sweep
+        stats = torch.empty((B, 4), dtype=torch.int32, device="cuda")
+        ps.scs_decode_mixed_split(pset, frames, sorder, n_two, Dmax, m["llr"], llr_off, info, info_off, pm, st,
+                                  stats=stats)
+        torch.cuda.synchronize()
+        ops_step = float((stats[:, 2].to(torch.int64) & 0xFFFFFFFF).sum().item())
+        del stats
+        bytes_step = float(sum(4 * int(n) for n in m["Ns"]) + 4 * int(m["words"].sum()) + 5 * B)
+        peaks = measured_peaks()
+        sms = ps.polar_device_info()["sm_count"]
+        alu_peak = sms * ALU_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6
+        t_alu, t_hbm = ops_step / alu_peak, bytes_step / (peaks["hbm_gbs"] * 1e9)
+        if t_alu >= t_hbm:
+            roof = {"bound": "alu", "achieved": ops_step / (ms_split / 1e3) / 1e12, "peak": alu_peak / 1e12,
+                    "unit": "Top/s"}
+        else:
+            roof = {"bound": "hbm", "achieved": bytes_step / (ms_split / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        out["roofline"] = roof
+        err = 0
+        info_np = info.cpu().numpy()
+        msg_np = m["msg"].cpu().numpy()
+        for b in range(0, B, max(1, B // 20000)):
+            lo = int(m["info_off"][b])
+            err += int(not np.array_equal(info_np[lo:lo + m["words"][b]], msg_np[lo:lo + m["words"][b]]))
+        out["fer_sampled"] = err / len(range(0, B, max(1, B // 20000)))
+    del m, per
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_mixed(args, rank: int, world: int, local_rank: int) -> None:
+    """The mixed workload on its own line: the batched path (two launches split
+    by stack rows, one graph) against one launch and per-configuration launches."""
+    import torch
+
+    import paper_1809_03606_gb300 as ps
+
+    torch.cuda.set_device(local_rank)
+    ps.load(build_if_missing=True)
+    B = int(args.frames) if args.frames else MIXED["frames"]
+    r = measure_mixed(args, B, rank, local_rank, args.steps, args.warmup, with_roofline=True)
+    cpu = mixed_cpu_baseline(args.cpu_frames * 4) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
-        line = {"metric": "decoded info Gbit/s (mixed batch)", "value": kmsg / (ms_mixed / 1e3) / 1e9, "unit": "Gbit/s",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
-                "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{B} mixed frames: N in {{128..2048}}, K/N in {{1/4,1/3,1/2,2/3,3/4}}, "
-                                       f"D in {{8,16,32,64}}, L = D, CRC-8, Eb/N0 ~ U[1,4] dB, shuffled",
-                           "codes": len(m["keys"]), "per_config_launches": len(per),
-                           "per_config_ms": ms_per, "per_config_gbps": kmsg / (ms_per / 1e3) / 1e9,
-                           "speedup_vs_per_config": ms_per / ms_mixed, "identical_outputs": same,
-                           "tuned": {"warps_per_block": wpb, "frames_per_claim": chunk},
-                           "fer_sampled": fer, "crc_fail_rate": float((st != 0).double().mean().item())},
-                "roofline": roof, "cpu_baseline": cpu, "clocks": sampler.summary() if sampler else None}
+        cfg = {"workload": f"{B} mixed frames: N in {{128..2048}}, K/N in {{1/4,1/3,1/2,2/3,3/4}}, "
+                           f"D in {{8,16,32,64}}, L = D, CRC-8, Eb/N0 ~ U[1,4] dB, shuffled"}
+        cfg.update({k: v for k, v in r.items() if k not in ("roofline", "clocks", "gbps")})
+        line = {"metric": "decoded info Gbit/s (mixed batch)", "value": r["gbps"], "unit": "Gbit/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["batched_ms"],
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic", "config": cfg,
+                "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"]}
         print(json.dumps(line), flush=True)
 
 
@@ -985,6 +1030,7 @@ def main(argv=None) -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lpt", action="store_true", help="mixed workload: claim frames in batch order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="sweep: skip the mixed-batch comparison object")
     ap.add_argument("--systematic", action="store_true", help="sweep: systematic encoding and decoding")
     args = ap.parse_args(argv)
     if args.warmup < 3:

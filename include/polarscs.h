@@ -245,6 +245,33 @@ int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_frames, const i
  * that expensive frames start first.  Errors: POLAR_EINVAL. */
 int polar_mixed_order(const polar_plan_set *set, const int32_t *h_frames, int B, int32_t *h_order);
 
+/* Claim order for scs_decode_mixed_split (host): the frames that need two
+ * stack rows a lane (valid descriptors with 32 < D <= 64) first, then all
+ * others, each part sorted like polar_mixed_order (decreasing N * (8 + D),
+ * ties in frame order).  *n_two receives the size of the first part.
+ * Errors: POLAR_EINVAL. */
+int polar_mixed_split_order(const polar_plan_set *set, const int32_t *h_frames, int B, int32_t *h_order, int *n_two);
+
+/* scs_decode_mixed in two persistent launches (a GPU mapping, not a
+ * construct of the paper; every frame's result is the one scs_decode_mixed
+ * gives): d_order[0, n_two) are decoded by the kernel with two stack rows a
+ * lane (D <= 64) on a second stream of the library, forked from `stream`
+ * with an event, and d_order[n_two, B) by the one-row kernel (D <= 32) on
+ * `stream`, which then waits for the other launch; so frames with D <= 32
+ * no longer carry the second row, and each launch fills the other's tail.
+ * d_order is required: polar_mixed_split_order gives it and n_two (a frame
+ * of the second part with D > 32 gets status 3, as an invalid descriptor).
+ * Dmax bounds the first part's D (it must exceed 32 when n_two > 0).  The
+ * side stream and its two events are made on the first call on a device
+ * (make it before any stream capture; later calls can be captured, the
+ * fork and join becoming graph dependencies).  Calls from several host
+ * threads are serialised while they enqueue.  Other arguments, outputs and
+ * errors as scs_decode_mixed. */
+int scs_decode_mixed_split(const polar_plan_set *set, const int32_t *d_frames, const int32_t *d_order, int B,
+                           int n_two, int Dmax, const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info,
+                           const int64_t *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
+                           void *stream);
+
 /* Autotuner for scs_decode_mixed: decodes the given batch (same arguments)
  * with every combination of 1, 2 or 4 warps (frames in flight) per block and
  * 1, 4 or 16 frames claimed per atomic, times each on the stream with CUDA

@@ -30,6 +30,7 @@ EXPORTED = (
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
     "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64", "polar_plan_set_scales", "polar_mixed_order",
     "polar_serve", "polar_serve_baseline", "polar_plan_set_systematic", "polar_plan_set_exact",
+    "polar_mixed_split_order", "scs_decode_mixed_split",
 )
 
 _lock = threading.Lock()
@@ -81,6 +82,8 @@ def load(build_if_missing: bool = False):
         lib.scs_decode_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.scs_tune_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.polar_mixed_order.argtypes = [vp, vp, i32, vp]
+        lib.polar_mixed_split_order.argtypes = [vp, vp, i32, vp, vp]
+        lib.scs_decode_mixed_split.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         i64, f64 = C.c_int64, C.c_double
         lib.polar_serve.argtypes = [vp, vp, vp, i32, vp, vp, i32, i64, f64, vp, vp, vp, vp, vp, vp]
         lib.polar_serve_baseline.argtypes = [vp, vp, vp, i32, vp, vp, i32, i64, f64, f64, vp, vp, vp, vp]
@@ -341,6 +344,31 @@ def scs_tune_mixed(pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_of
     return w.value, c.value
 
 
+def polar_mixed_split_order(pset: PlanSet, frames_host: np.ndarray):
+    """Claim order for scs_decode_mixed_split (host): (order, n_two), the
+    frames needing two stack rows (D > 32) first."""
+    fr = np.ascontiguousarray(frames_host, dtype=np.int32)
+    out = np.zeros(fr.shape[0], np.int32)
+    n_two = C.c_int(0)
+    _check("polar_mixed_split_order", load().polar_mixed_split_order(pset.handle, _np_ptr(fr), fr.shape[0],
+                                                                     _np_ptr(out), C.byref(n_two)))
+    return out, n_two.value
+
+
+def scs_decode_mixed_split(pset: PlanSet, frames, order, n_two: int, Dmax: int, llr, llr_off, info, info_off, pm,
+                           status, stats=None, stream=None) -> None:
+    """The mixed batch in two launches split by stack rows (see polarscs.h);
+    ``order`` and ``n_two`` come from polar_mixed_split_order."""
+    import torch
+
+    B = frames.shape[0]
+    args = _mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status, order)
+    # _mixed_args gives (set, frames, order, B, Dmax, llr, llr_off, info, info_off, pm, status)
+    _check("scs_decode_mixed_split", load().scs_decode_mixed_split(
+        args[0], args[1], args[2], args[3], int(n_two), *args[4:],
+        None if stats is None else _dev_ptr(stats, torch.int32, "stats", (B, 4)), _stream_ptr(stream)))
+
+
 def polar_mixed_order(pset: PlanSet, frames_host: np.ndarray) -> np.ndarray:
     """Longest-first claim order (host) for a [B, 4] int32 descriptor array."""
     fr = np.ascontiguousarray(frames_host, dtype=np.int32)
@@ -370,6 +398,8 @@ class MixedBatch:
         self.Dmax = int(fr[:, 1].max()) if B else 1
         self.frames = torch.from_numpy(fr).to(device)
         self.order = torch.from_numpy(polar_mixed_order(pset, fr)).to(device) if B else None
+        split, self.n_two = polar_mixed_split_order(pset, fr) if B else (np.zeros(0, np.int32), 0)
+        self.split_order = torch.from_numpy(split).to(device) if B else None
         if isinstance(llr_rows, np.ndarray) and llr_rows.ndim == 1:
             flat = llr_rows.astype(np.float32, copy=False)
         else:
@@ -385,6 +415,11 @@ class MixedBatch:
     def decode(self, pset: PlanSet, stats=None, stream=None) -> None:
         scs_decode_mixed(pset, self.frames, self.Dmax, self.llr, self.llr_off, self.info, self.info_off, self.pm,
                          self.status, stats, stream, self.order)
+
+    def decode_split(self, pset: PlanSet, stats=None, stream=None) -> None:
+        """The same batch in two launches split by stack rows (scs_decode_mixed_split)."""
+        scs_decode_mixed_split(pset, self.frames, self.split_order, self.n_two, self.Dmax, self.llr, self.llr_off,
+                               self.info, self.info_off, self.pm, self.status, stats, stream)
 
     def tune(self, pset: PlanSet, stream=None):
         return scs_tune_mixed(pset, self.frames, self.Dmax, self.llr, self.llr_off, self.info, self.info_off, self.pm,

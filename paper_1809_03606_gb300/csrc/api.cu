@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <new>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "plan.h"
@@ -24,7 +25,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
 int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, const int *d_order, int B, int Dmax,
                             const float *d_llr, const long long *d_llr_off, uint32_t *d_info,
                             const long long *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
-                            cudaStream_t stream, int wpb_req, int chunk_req);
+                            cudaStream_t stream, int wpb_req, int chunk_req, int nframes);
 void free_set_device(polar_plan_set *set);
 template <typename T>
 int launch_gsc(const polar_plan *p, const uint8_t *d_info_mask, const T *d_llr, const uint32_t *d_u, int B,
@@ -213,7 +214,65 @@ extern "C" int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_fram
     return launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), d_order, B, Dmax, d_llr,
                                    reinterpret_cast<const long long *>(d_llr_off), d_info,
                                    reinterpret_cast<const long long *>(d_info_off), d_pm, d_status, d_stats,
-                                   cudaStream_t(stream), 0, 0);
+                                   cudaStream_t(stream), 0, 0, B);
+}
+
+// the side stream and fork/join events of scs_decode_mixed_split, one set
+// per device, made on the first call there; the mutex serialises the
+// enqueueing of calls that share them
+namespace {
+struct SplitStreams {
+    bool ready = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_split_mu;
+SplitStreams g_split[64];
+}  // namespace
+
+extern "C" int scs_decode_mixed_split(const polar_plan_set *set, const int32_t *d_frames, const int32_t *d_order,
+                                      int B, int n_two, int Dmax, const float *d_llr, const int64_t *d_llr_off,
+                                      uint32_t *d_info, const int64_t *d_info_off, float *d_pm, int8_t *d_status,
+                                      uint32_t *d_stats, void *stream) {
+    int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
+    if (rc || B == 0) return rc;
+    if (!d_order || n_two < 0 || n_two > B || (n_two > 0 && Dmax <= 32)) return POLAR_EINVAL;
+    const int4 *fr = reinterpret_cast<const int4 *>(d_frames);
+    const long long *lo = reinterpret_cast<const long long *>(d_llr_off);
+    const long long *io = reinterpret_cast<const long long *>(d_info_off);
+    cudaStream_t s = cudaStream_t(stream);
+    const int Dmax1 = std::min(Dmax, 32);
+    if (n_two == 0 || n_two == B) {  // one kind of frame only: one launch
+        return launch_scs_decode_mixed(set, fr, d_order, B, n_two ? Dmax : Dmax1, d_llr, lo, d_info, io, d_pm,
+                                       d_status, d_stats, s, 0, 0, B);
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(g_split_mu);
+    SplitStreams &ss = g_split[dev];
+    if (!ss.ready) {
+        e = cudaStreamCreateWithFlags(&ss.side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_status(e);
+        ss.ready = true;
+    }
+    // the two-row frames (order[0, n_two)) on the side stream, the one-row
+    // frames (order[n_two, B)) on the caller's stream, joined back to it
+    e = cudaEventRecord(ss.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.side, ss.fork, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = launch_scs_decode_mixed(set, fr, d_order, n_two, Dmax, d_llr, lo, d_info, io, d_pm, d_status, d_stats,
+                                 ss.side, 0, 0, B);
+    const int rc2 = launch_scs_decode_mixed(set, fr, d_order + n_two, B - n_two, Dmax1, d_llr, lo, d_info, io, d_pm,
+                                            d_status, d_stats, s, 0, 0, B);
+    e = cudaEventRecord(ss.join, ss.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ss.join, 0);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    return e == cudaSuccess ? 0 : cuda_status(e);
 }
 
 extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, const int32_t *d_order, int B, int Dmax,
@@ -243,7 +302,7 @@ extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, cons
                 rc = launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), d_order, B, Dmax, d_llr,
                                              reinterpret_cast<const long long *>(d_llr_off), d_info,
                                              reinterpret_cast<const long long *>(d_info_off), d_pm, d_status, nullptr,
-                                             s, kWpb[wi], kChunk[ci]);
+                                             s, kWpb[wi], kChunk[ci], B);
                 cudaEventRecord(e1, s);
                 e = cudaEventSynchronize(e1);
                 if (e != cudaSuccess) rc = cuda_status(e);
@@ -318,6 +377,28 @@ extern "C" int polar_mixed_order(const polar_plan_set *set, const int32_t *h_fra
     }
     std::stable_sort(key.begin(), key.end());
     for (int b = 0; b < B; ++b) h_order[b] = key[size_t(b)].second;
+    return 0;
+}
+
+// The claim order of scs_decode_mixed_split (host): the frames that need two
+// stack rows a lane (valid descriptors with D > 32) first, then the others,
+// each part longest-first like polar_mixed_order; *n_two = the first part's size.
+extern "C" int polar_mixed_split_order(const polar_plan_set *set, const int32_t *h_frames, int B, int32_t *h_order,
+                                       int *n_two) {
+    if (!set || B < 0 || !n_two || (B > 0 && (!h_frames || !h_order))) return POLAR_EINVAL;
+    std::vector<std::pair<std::pair<int, long long>, int>> key(static_cast<size_t>(B));
+    int two = 0;
+    for (int b = 0; b < B; ++b) {
+        const int pi = h_frames[4 * size_t(b)], D = h_frames[4 * size_t(b) + 1];
+        const bool ok = pi >= 0 && pi < int(set->plans.size());
+        const long long w = ok ? (long long)set->plans[size_t(pi)]->N * (8 + std::max(D, 0)) : 0;
+        const int part = (ok && D > 32 && D <= POLAR_MAX_D_GPU) ? 0 : 1;
+        two += part == 0;
+        key[size_t(b)] = {{part, -w}, b};
+    }
+    std::stable_sort(key.begin(), key.end());
+    for (int b = 0; b < B; ++b) h_order[b] = key[size_t(b)].second;
+    *n_two = two;
     return 0;
 }
 

@@ -81,6 +81,7 @@ struct Args {
     int ncodes;
     const int4 *frames;         // mixed: (code index, D, L, unused) per frame
     const int *order;           // mixed: claim k decodes frame order[k] (null: k)
+    int nframes;                // mixed: frames of the whole batch (order entries below it are decoded)
     const long long *llr_off;   // mixed: index of frame b's first LLR
     const long long *info_off;  // mixed: index of frame b's first message word
     int Dmax;                   // mixed: largest D the scratch was sized for
@@ -1371,7 +1372,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
         const unsigned b1 = min(unsigned(a.B), b0 + unsigned(a.chunk));
         for (unsigned k = b0; k < b1; ++k) {
             const unsigned b = (MIXED && a.order) ? unsigned(__ldg(a.order + k)) : k;
-            if (MIXED && b >= unsigned(a.B)) continue;
+            if (MIXED && b >= unsigned(a.nframes)) continue;
             if constexpr (!MIXED) {
                 const Code &c = a.code;
                 Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
@@ -1669,10 +1670,11 @@ void free_set_device(polar_plan_set *set) {
     set->device = -1;
 }
 
+// B claims over d_order (null: frames 0 .. B-1) of a batch of nframes frames
 int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, const int *d_order, int B, int Dmax,
                             const float *d_llr, const long long *d_llr_off, uint32_t *d_info,
                             const long long *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
-                            cudaStream_t stream, int wpb_req, int chunk_req) {
+                            cudaStream_t stream, int wpb_req, int chunk_req, int nframes) {
     if (B == 0) return 0;
     const Code *codes = nullptr;
     int wpb_pref, chunk;
@@ -1688,6 +1690,7 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     a.ncodes = int(set->plans.size());
     a.frames = d_frames;
     a.order = d_order;
+    a.nframes = nframes;
     a.llr_off = d_llr_off;
     a.info_off = d_info_off;
     a.Dmax = Dmax;

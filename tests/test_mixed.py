@@ -1,6 +1,7 @@
 """Mixed batches: frames of different codes, stack depths and visit caps in
-one persistent launch (scs_decode_mixed).  Each frame must come out exactly
-as if it had been decoded alone with its own plan, D and L."""
+one persistent launch (scs_decode_mixed), or in two launches split by stack
+rows (scs_decode_mixed_split).  Each frame must come out exactly as if it
+had been decoded alone with its own plan, D and L."""
 import ctypes as C
 
 import numpy as np
@@ -34,6 +35,30 @@ def test_plan_set_validation(lib):
     assert lib.scs_decode_mixed(*args(4, 0, d)) == ps.POLAR_EINVAL
     assert lib.scs_decode_mixed(*args(4, 8, C.c_void_p(260))) == ps.POLAR_EINVAL  # frames not 16-byte aligned
     assert lib.scs_decode_mixed(*args(0, 8, d)) == 0
+
+
+def test_split_order_and_validation(lib):
+    """polar_mixed_split_order: frames with 32 < D <= 64 first (longest first
+    within each part), invalid descriptors with the one-row part; the split
+    decode rejects a missing order, n_two outside [0, B] and a Dmax that
+    cannot hold the two-row part."""
+    p1 = ps.Plan(64, 32, ps.polar_construct(64, 32, 0.0))
+    p2 = ps.Plan(256, 128, ps.polar_construct(256, 128, 0.0))
+    s = ps.PlanSet([p1, p2])
+    fr = np.array([[0, 8, 8, 0], [1, 40, 40, 0], [0, 64, 64, 0], [1, 32, 32, 0], [5, 64, 64, 0], [1, 33, 1, 0]],
+                  np.int32)
+    order, n_two = ps.polar_mixed_split_order(s, fr)
+    assert n_two == 3
+    assert sorted(order[:3].tolist()) == [1, 2, 5] and sorted(order[3:].tolist()) == [0, 3, 4]
+    assert order[:3].tolist() == [1, 5, 2]  # 256*(8+40) > 256*(8+33) > 64*(8+64)
+    assert order[3:].tolist() == [3, 0, 4]  # the invalid descriptor (plan 5) weighs 0: last
+    d = C.c_void_p(256)
+    args = lambda order, n, Dmax: (s.handle, d, order, 6, n, Dmax, d, d, d, d, d, d, None, None)
+    assert lib.scs_decode_mixed_split(*args(None, 3, 64)) == ps.POLAR_EINVAL
+    assert lib.scs_decode_mixed_split(*args(d, 7, 64)) == ps.POLAR_EINVAL
+    assert lib.scs_decode_mixed_split(*args(d, -1, 64)) == ps.POLAR_EINVAL
+    assert lib.scs_decode_mixed_split(*args(d, 3, 32)) == ps.POLAR_EINVAL
+    assert lib.scs_decode_mixed_split(*args(d, 3, 65)) == ps.POLAR_ELIMIT
 
 
 # ----------------------------------------------------------------- GPU tests
@@ -198,3 +223,56 @@ def test_mixed_with_systematic_plans(lib, oracle_lib):
         got = ps.unpack_bits(mb.message_words(b)[None, :], K - crc)[0]
         assert np.array_equal(got, m_o), b
         assert pm[b].view(np.uint32) == pm_o.view(np.uint32) and st[b] == st_o, b
+
+
+@pytest.mark.gpu
+def test_split_launches_equal_one_launch_and_oracle(lib, oracle_lib):
+    """The batch split by stack rows into two launches on two streams gives
+    every frame exactly the one-launch result (message words, metric bits,
+    status, counters), which is also the oracle's on a sample; the split is
+    captured in a CUDA graph and replayed; batches with only one kind of
+    frame take a single launch."""
+    torch = pytest.importorskip("torch")
+    plans, frozens, idx, D, L, rows, msgs = _mixed_problem(oracle_lib, CODES, 3000, seed=25)
+    pset = ps.PlanSet(plans)
+    mb = ps.MixedBatch(pset, idx, D, L, rows)
+    assert 0 < mb.n_two < mb.B
+    stats1 = torch.empty((mb.B, 4), dtype=torch.int32, device="cuda")
+    mb.decode(pset, stats1)
+    torch.cuda.synchronize()
+    ref = (mb.info.clone(), mb.pm.clone(), mb.status.clone(), stats1.clone())
+    mb.info.zero_()
+    mb.pm.zero_()
+    stats2 = torch.zeros_like(stats1)
+    mb.decode_split(pset, stats2)
+    torch.cuda.synchronize()
+    for r, g in zip(ref, (mb.info, mb.pm, mb.status, stats2)):
+        assert torch.equal(r, g)
+    pm, st = mb.pm.cpu().numpy(), mb.status.cpu().numpy()
+    for b in range(0, mb.B, 15):
+        N, K, crc = CODES[idx[b]]
+        st_o, m_o, pm_o, _, _ = oracle_lib.scs_decode(rows[b], N, K, frozens[idx[b]], fast=True, D=int(D[b]),
+                                                      L=int(L[b]), crc_len=crc)
+        got = ps.unpack_bits(mb.message_words(b)[None, :], K - crc)[0]
+        assert np.array_equal(got, m_o) and pm[b].view(np.uint32) == pm_o.view(np.uint32) and st[b] == st_o
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        mb.decode_split(pset)
+    for _ in range(2):
+        mb.info.zero_()
+        mb.pm.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for r, x in zip(ref[:3], (mb.info, mb.pm, mb.status)):
+            assert torch.equal(r, x)
+    for keep in (D <= 32, D > 32):  # one kind of frame only
+        sel = np.nonzero(keep)[0][:500]
+        one = ps.MixedBatch(pset, idx[sel], D[sel], L[sel], [rows[b] for b in sel])
+        assert one.n_two in (0, one.B)
+        one.decode(pset)
+        torch.cuda.synchronize()
+        r1 = (one.info.clone(), one.pm.clone(), one.status.clone())
+        one.decode_split(pset)
+        torch.cuda.synchronize()
+        for r, x in zip(r1, (one.info, one.pm, one.status)):
+            assert torch.equal(r, x)
