@@ -960,12 +960,20 @@ def bench_serve(args, rank: int, world: int, local_rank: int) -> None:
         t_end = out["report"]["seconds_to_last_completion"]
         R = arr.size
         bits = float(kmsg_pool[p[ok]].sum())
-        return {"requests": int(R), "completed": int(ok.sum()), "seconds": t_end,
+        res = {"requests": int(R), "completed": int(ok.sum()), "seconds": t_end,
                 "throughput_req_s": float(ok.sum()) / t_end if t_end > 0 else None,
                 "info_gbps": bits / t_end / 1e9 if t_end > 0 else None,
                 "p50_ms": float(np.percentile(lat[ok], 50) * 1e3) if ok.any() else None,
                 "p99_ms": float(np.percentile(lat[ok], 99) * 1e3) if ok.any() else None,
                 "report": out["report"]}
+        svc = out.get("service")
+        if svc is not None and ok.any():
+            wait_ = lat[ok] - svc[ok]
+            res.update({"p50_service_ms": float(np.percentile(svc[ok], 50) * 1e3),
+                        "p99_service_ms": float(np.percentile(svc[ok], 99) * 1e3),
+                        "p50_wait_ms": float(np.percentile(wait_, 50) * 1e3),
+                        "p99_wait_ms": float(np.percentile(wait_, 99) * 1e3)})
+        return res
 
     arena = SERVE["arena_bytes"] // 4
     wait = max(60.0, 4 * seconds)

@@ -332,13 +332,16 @@ int gsc_loss_grad_f64(const polar_plan *plan, const double *d_llr, const uint32_
  * Outputs per request: pm_out, status_out (as scs_decode_batch; 127 if never
  * decoded), latency_out (completion - arrival, seconds; NaN if not completed)
  * and, for polar_serve, the packed message words at info_off[r] of info_out
- * (both may be NULL).  report (6 doubles): seconds from start to the last
+ * (both may be NULL) and service_out (may be NULL): the seconds from the
+ * moment a warp starts the request, after its release, to its completion,
+ * both on the device clock (latency - service = waiting for release and for
+ * a warp).  report (6 doubles): seconds from start to the last
  * completion, arena-full stalls, error flag, most requests in flight (serve) or
  * launches (baseline), requests completed, arena bytes. */
 int polar_serve(const polar_plan_set *set, const int32_t *req, const double *arrival_s, int R, const float *pool_llr,
                 const int64_t *pool_off, int P, int64_t arena_floats, double wait_s, float *pm_out,
                 int8_t *status_out, uint32_t *info_out, const int64_t *info_off, double *latency_out,
-                double *report);
+                double *service_out, double *report);
 int polar_serve_baseline(const polar_plan_set *set, const int32_t *req, const double *arrival_s, int R,
                          const float *pool_llr, const int64_t *pool_off, int P, int64_t arena_floats,
                          double interval_s, double wait_s, float *pm_out, int8_t *status_out, double *latency_out,

@@ -85,7 +85,7 @@ def load(build_if_missing: bool = False):
         lib.polar_mixed_split_order.argtypes = [vp, vp, i32, vp, vp]
         lib.scs_decode_mixed_split.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         i64, f64 = C.c_int64, C.c_double
-        lib.polar_serve.argtypes = [vp, vp, vp, i32, vp, vp, i32, i64, f64, vp, vp, vp, vp, vp, vp]
+        lib.polar_serve.argtypes = [vp, vp, vp, i32, vp, vp, i32, i64, f64, vp, vp, vp, vp, vp, vp, vp]
         lib.polar_serve_baseline.argtypes = [vp, vp, vp, i32, vp, vp, i32, i64, f64, f64, vp, vp, vp, vp]
         for fn in (lib.gsc_loss, lib.gsc_loss_f64):
             fn.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
@@ -535,12 +535,14 @@ def _serve_inputs(req, arrival_s, pool_llr, pool_off):
 def polar_serve(pset: PlanSet, req, arrival_s, pool_llr, pool_off, arena_floats: int, wait_s: float = 30.0,
                 info_off=None) -> dict:
     """Continuous-batching engine (see polarscs.h).  Returns per-request pm,
-    status, latency (s), optional message words, and the engine report."""
+    status, latency (s), service time (s, a warp's start to completion),
+    optional message words, and the engine report."""
     req, arr, pool, poff = _serve_inputs(req, arrival_s, pool_llr, pool_off)
     R = req.shape[0]
     pm = np.zeros(R, np.float32)
     st = np.zeros(R, np.int8)
     lat = np.zeros(R, np.float64)
+    svc = np.zeros(R, np.float64)
     rep = np.zeros(6, np.float64)
     info = ioff = None
     if info_off is not None:
@@ -550,8 +552,8 @@ def polar_serve(pset: PlanSet, req, arrival_s, pool_llr, pool_off, arena_floats:
     rc = load().polar_serve(pset.handle, _np_ptr(req), _np_ptr(arr), R, _np_ptr(pool), _np_ptr(poff), poff.size,
                             int(arena_floats), float(wait_s), _np_ptr(pm), _np_ptr(st),
                             None if info is None else _np_ptr(info), None if ioff is None else _np_ptr(ioff),
-                            _np_ptr(lat), _np_ptr(rep))
-    out = dict(rc=rc, pm=pm, status=st, latency=lat, info=info, report=dict(zip(_REPORT, rep.tolist())))
+                            _np_ptr(lat), _np_ptr(svc), _np_ptr(rep))
+    out = dict(rc=rc, pm=pm, status=st, latency=lat, service=svc, info=info, report=dict(zip(_REPORT, rep.tolist())))
     if rc < 0 and rc != POLAR_ETIMEOUT:
         raise PolarError("polar_serve", rc)
     return out

@@ -102,6 +102,7 @@ struct Args {
     const int *abort_flag;           // host-mapped: stop waiting
     unsigned char *done_flag;        // host-mapped: 1 when request k is complete
     unsigned long long *t_done;      // device: %globaltimer at completion
+    unsigned long long *t_start;     // device: %globaltimer when a warp starts the request
     int *error_flag;                 // device: a wait ran out
     unsigned long long wait_ns;      // longest wait for one request
     long long serve_stage_off;       // words into a warp's scratch where its LLR staging starts
@@ -1451,6 +1452,7 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
         k = __shfl_sync(FULL, k, 0);
         ok = __shfl_sync(FULL, ok, 0);
         if (k >= unsigned(a.B) || !ok) break;
+        if (lane == 0) a.t_start[k] = global_ns();
         const int4 fd = a.frames[k];
         if (fd.x < 0 || fd.x >= a.ncodes || fd.y < 1 || fd.y > a.Dmax || fd.z < 1 || fd.z > 255) {
             if (lane == 0) {
@@ -1744,9 +1746,9 @@ int serve_codes(const polar_plan_set *set, const void **out) {
 int launch_scs_serve(const polar_plan_set *set, const void *codes_v, const int4 *d_frames, int B, int Dmax,
                      const float *d_arena, const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off,
                      float *d_pm, int8_t *d_status, const unsigned long long *d_head, const int *h_abort,
-                     unsigned char *h_done, unsigned long long *d_t_done, int *d_error, unsigned long long wait_ns,
-                     unsigned *d_counter, uint32_t *d_scratch, size_t scratch_bytes, int wpb_pref,
-                     cudaStream_t stream) {
+                     unsigned char *h_done, unsigned long long *d_t_done, unsigned long long *d_t_start, int *d_error,
+                     unsigned long long wait_ns, unsigned *d_counter, uint32_t *d_scratch, size_t scratch_bytes,
+                     int wpb_pref, cudaStream_t stream) {
     const Code *codes = static_cast<const Code *>(codes_v);
     Args a{};
     a.codes = codes;
@@ -1769,6 +1771,7 @@ int launch_scs_serve(const polar_plan_set *set, const void *codes_v, const int4 
     a.abort_flag = h_abort;
     a.done_flag = h_done;
     a.t_done = d_t_done;
+    a.t_start = d_t_start;
     a.error_flag = d_error;
     a.wait_ns = wait_ns;
     a.counter = d_counter;

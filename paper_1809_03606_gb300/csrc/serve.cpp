@@ -39,9 +39,9 @@ int serve_codes(const polar_plan_set *set, const void **out);
 int launch_scs_serve(const polar_plan_set *set, const void *codes, const int4 *d_frames, int B, int Dmax,
                      const float *d_arena, const long long *d_llr_off, uint32_t *d_info, const long long *d_info_off,
                      float *d_pm, int8_t *d_status, const unsigned long long *d_head, const int *h_abort,
-                     unsigned char *h_done, unsigned long long *d_t_done, int *d_error, unsigned long long wait_ns,
-                     unsigned *d_counter, uint32_t *d_scratch, size_t scratch_bytes, int wpb_pref,
-                     cudaStream_t stream);
+                     unsigned char *h_done, unsigned long long *d_t_done, unsigned long long *d_t_start, int *d_error,
+                     unsigned long long wait_ns, unsigned *d_counter, uint32_t *d_scratch, size_t scratch_bytes,
+                     int wpb_pref, cudaStream_t stream);
 size_t serve_scratch_bytes(const polar_plan_set *set, int Dmax);
 int read_device_ns(unsigned long long *d_out, cudaStream_t s);
 int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *d_llr, int B, int D, int L,
@@ -115,7 +115,7 @@ int make_layout(const polar_plan_set *set, const int32_t *req, int R, long long 
 extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const double *arrival_s, int R,
                            const float *pool_llr, const int64_t *pool_off, int P, int64_t arena_floats,
                            double wait_s, float *pm_out, int8_t *status_out, uint32_t *info_out,
-                           const int64_t *info_off, double *latency_out, double *report) {
+                           const int64_t *info_off, double *latency_out, double *service_out, double *report) {
     if (!set || !req || !arrival_s || R < 1 || !pool_llr || !pool_off || P < 1 || arena_floats < 1 || !pm_out ||
         !status_out || !latency_out || !report || wait_s <= 0.0)
         return POLAR_EINVAL;
@@ -150,16 +150,18 @@ extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const 
         for (int r = 0; r < R; ++r) out_words = std::max(out_words, ioff[size_t(r)] + lay.words[size_t(r)]);
 
     cudaError_t e = cudaSuccess;
-    DevBuf d_arena, d_frames, d_loff, d_ioff, d_info, d_pm, d_st, d_tdone, d_head, d_err, d_cnt, d_scr, d_gt;
-    HostBuf h_done, h_abort, h_head, h_tdone, h_mirror;
+    DevBuf d_arena, d_frames, d_loff, d_ioff, d_info, d_pm, d_st, d_tdone, d_tstart, d_head, d_err, d_cnt, d_scr, d_gt;
+    HostBuf h_done, h_abort, h_head, h_tdone, h_tstart, h_mirror;
     const size_t scr_bytes = serve_scratch_bytes(set, Dmax);
     if ((e = d_arena.alloc(size_t(arena_floats) * 4)) != cudaSuccess || (e = d_frames.alloc(sizeof(int4) * R)) ||
         (e = d_loff.alloc(8 * size_t(R))) || (e = d_ioff.alloc(8 * size_t(R))) ||
         (e = d_info.alloc(4 * size_t(out_words))) || (e = d_pm.alloc(4 * size_t(R))) || (e = d_st.alloc(size_t(R))) ||
-        (e = d_tdone.alloc(8 * size_t(R))) || (e = d_head.alloc(8)) || (e = d_err.alloc(4)) || (e = d_cnt.alloc(4)) ||
+        (e = d_tdone.alloc(8 * size_t(R))) || (e = d_tstart.alloc(8 * size_t(R))) || (e = d_head.alloc(8)) ||
+        (e = d_err.alloc(4)) || (e = d_cnt.alloc(4)) ||
         (e = d_scr.alloc(scr_bytes)) || (e = d_gt.alloc(8)) || (e = h_done.alloc(size_t(R), cudaHostAllocMapped)) ||
         (e = h_abort.alloc(4, cudaHostAllocMapped)) || (e = h_head.alloc(8 * 4096, 0)) ||
-        (e = h_tdone.alloc(8 * size_t(R), 0)) || (e = h_mirror.alloc(size_t(arena_floats) * 4, 0)))
+        (e = h_tdone.alloc(8 * size_t(R), 0)) || (e = h_tstart.alloc(8 * size_t(R), 0)) ||
+        (e = h_mirror.alloc(size_t(arena_floats) * 4, 0)))
         return cuda_status(e);
     float *mirror = static_cast<float *>(h_mirror.p);
     volatile unsigned char *done = static_cast<volatile unsigned char *>(h_done.p);
@@ -218,7 +220,8 @@ extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const 
                           static_cast<uint32_t *>(d_info.p), static_cast<const long long *>(d_ioff.p),
                           static_cast<float *>(d_pm.p), static_cast<int8_t *>(d_st.p),
                           static_cast<const unsigned long long *>(d_head.p), d_abort, d_done,
-                          static_cast<unsigned long long *>(d_tdone.p), static_cast<int *>(d_err.p),
+                          static_cast<unsigned long long *>(d_tdone.p), static_cast<unsigned long long *>(d_tstart.p),
+                          static_cast<int *>(d_err.p),
                           (unsigned long long)(wait_s * 1e9), static_cast<unsigned *>(d_cnt.p),
                           static_cast<uint32_t *>(d_scr.p), scr_bytes, 0, ks);
     if (rc) {
@@ -299,18 +302,22 @@ extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const 
     if (es == cudaSuccess) es = cudaMemcpy(pm_out, d_pm.p, 4 * size_t(R), cudaMemcpyDeviceToHost);
     if (es == cudaSuccess) es = cudaMemcpy(status_out, d_st.p, size_t(R), cudaMemcpyDeviceToHost);
     if (es == cudaSuccess) es = cudaMemcpy(h_tdone.p, d_tdone.p, 8 * size_t(R), cudaMemcpyDeviceToHost);
+    if (es == cudaSuccess) es = cudaMemcpy(h_tstart.p, d_tstart.p, 8 * size_t(R), cudaMemcpyDeviceToHost);
     if (es == cudaSuccess && info_out) es = cudaMemcpy(info_out, d_info.p, 4 * size_t(out_words), cudaMemcpyDeviceToHost);
     cleanup();
     if (es != cudaSuccess) return cuda_status(es);
     const unsigned long long *td = static_cast<const unsigned long long *>(h_tdone.p);
+    const unsigned long long *ts = static_cast<const unsigned long long *>(h_tstart.p);
     const double start_off = std::chrono::duration<double>(t_start - h0).count();  // host start relative to gt0
     double last = 0.0;
     int completed = 0;
     for (int r = 0; r < R; ++r) {
         if (!done[r]) {
             latency_out[r] = std::nan("");
+            if (service_out) service_out[r] = std::nan("");
             continue;
         }
+        if (service_out) service_out[r] = double((long long)(td[r] - ts[r])) * 1e-9;  // on the device clock
         ++completed;
         const double t_done_s = double((long long)(td[r] - gt0)) * 1e-9 - start_off;  // since t_start
         latency_out[r] = t_done_s - arrival_s[r];

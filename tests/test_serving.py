@@ -91,6 +91,8 @@ def test_served_results_equal_oracle_and_solo_under_arena_pressure(pool, oracle_
     assert out["rc"] == 0 and out["report"]["completed"] == R
     assert out["report"]["arena_full_stalls"] > 0  # admission by memory really happened
     assert np.all(out["latency"] >= 0)
+    # service time (a warp's start to completion, device clock) within latency
+    assert np.all(out["service"] > 0) and np.all(out["service"] <= out["latency"] + 1e-4)
     for r in range(R):
         pm_s, st_s, info_s = solo[int(p[r])]
         m_o, pm_o, st_o = ref[int(p[r])]
