@@ -436,7 +436,9 @@ def bench_e2e(ps, plan, llrs, w, args, world: int):
     """Same metric through the C ABI with host buffers: every step copies its
     LLRs from pinned host memory and reads the results back, in chunks whose
     copies overlap the decode of the previous chunk; consecutive chunks decode
-    on two streams, so the tail of one launch overlaps the next."""
+    on two streams, so the tail of one launch overlaps the next.  (Chunks of a
+    whole Eb/N0 point measured slower, 1.35 against 1.39 Gbit/s: a 4 GiB copy
+    does not hide behind the short decode of the 3.0 dB point.)"""
     import torch
 
     B, N = w["frames"], w["N"]

@@ -87,7 +87,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 // LOGN > 0: the code length 2^LOGN fixed at compile time (every index shift
 // and trip count a constant); LOGN = 0: any length
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
+__global__ void __launch_bounds__(kGscThreads, 4) gsc_kernel(GscArgs<T> a) {
     extern __shared__ __align__(16) unsigned char gsm[];
     const int N = LOGN ? (1 << LOGN) : a.N, n = LOGN ? LOGN : a.n, W = LOGN ? ((N + 31) >> 5) : a.W;
     const int half = N >> 1;
@@ -108,6 +108,14 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
     // lane, the others two adjacent node pairs per thread (each thread's one
     // share of the warp's 64 or the block's 512 pairs)
     constexpr bool kVec = sizeof(T) == 4 && LOGN == 10 && kGscThreads == 256;
+    // shared-memory position of index p of stage st: in the specialised
+    // kernel stages 2-5 -- the ones the two node pairs a thread takes at
+    // stages 2-4 read and write -- have the 4-value groups of the second
+    // 32-value half of every 64 values permuted (bits 2-4 XOR 28), so that
+    // those accesses hit 32 distinct banks per half-warp; 4-value groups stay
+    // whole and aligned for the vector accesses.  The stage loops are
+    // unrolled, so the stage is a constant and the other stages pay nothing.
+    auto sw = [](int st, int p) { return (kVec && st >= 2 && st <= 5) ? (p ^ (((p >> 5) & 1) * 28)) : p; };
     // the specialised kernel loads the next frame's LLR row into registers
     // while the current frame is computed (N / 256 values per thread)
     constexpr int kPre = LOGN ? ((1 << LOGN) + kGscThreads - 1) / kGscThreads : 1;
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
             if constexpr (kVec) {
                 if (lam <= 1) {  // two node pairs per lane in one 16-byte access
                 const int p = wid * seg + 4 * lane;
-                const float4 v = *reinterpret_cast<const float4 *>(par + p);
+                const float4 v = *reinterpret_cast<const float4 *>(par + sw(lam + 1, p));
                 const uint32_t w = bx[p >> 5] >> (p & 31);
                 float4 o;
                 if (lam == 0) {  // pairs (p, p+1), (p+2, p+3)
@@ -185,19 +193,19 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
                     fwd_pair<T>(v.x, v.z, w & 1u, s, o.x, o.z);
                     fwd_pair<T>(v.y, v.w, (w >> 1) & 1u, s, o.y, o.w);
                 }
-                *reinterpret_cast<float4 *>(cur + p) = o;
+                *reinterpret_cast<float4 *>(cur + sw(lam, p)) = o;
                 done = true;
                 } else {  // two adjacent node pairs per thread in 8-byte accesses
                     const int i = 2 * (loc ? wid * 32 + lane : tid);
                     const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
-                    const float2 x = *reinterpret_cast<const float2 *>(par + ps + j);
-                    const float2 y = *reinterpret_cast<const float2 *>(par + ps + len + j);
+                    const float2 x = *reinterpret_cast<const float2 *>(par + sw(lam + 1, ps + j));
+                    const float2 y = *reinterpret_cast<const float2 *>(par + sw(lam + 1, ps + len + j));
                     const uint32_t w = bx[(ps + j) >> 5] >> ((ps + j) & 31);
                     float2 l, r;
                     fwd_pair<T>(x.x, y.x, w & 1u, s, l.x, r.x);
                     fwd_pair<T>(x.y, y.y, (w >> 1) & 1u, s, l.y, r.y);
-                    *reinterpret_cast<float2 *>(cur + ps + j) = l;
-                    *reinterpret_cast<float2 *>(cur + ps + len + j) = r;
+                    *reinterpret_cast<float2 *>(cur + sw(lam, ps + j)) = l;
+                    *reinterpret_cast<float2 *>(cur + sw(lam, ps + len + j)) = r;
                     done = true;
                 }
             }
@@ -248,8 +256,8 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
                 if constexpr (kVec) {
                     if (lam <= 1) {  // two node pairs per lane in 16-byte accesses
                     const int p = wid * seg + 4 * lane;
-                    const float4 v = *reinterpret_cast<const float4 *>(par + p);
-                    const float4 c = *reinterpret_cast<const float4 *>(cur + p);
+                    const float4 v = *reinterpret_cast<const float4 *>(par + sw(lam + 1, p));
+                    const float4 c = *reinterpret_cast<const float4 *>(cur + sw(lam, p));
                     const uint32_t w = bx[p >> 5] >> (p & 31);
                     float4 o;
                     if (lam == 0) {
@@ -259,21 +267,21 @@ __global__ void __launch_bounds__(kGscThreads) gsc_kernel(GscArgs<T> a) {
                         bwd_pair<T>(v.x, v.z, c.x, c.z, w & 1u, s, gs, o.x, o.z);
                         bwd_pair<T>(v.y, v.w, c.y, c.w, (w >> 1) & 1u, s, gs, o.y, o.w);
                     }
-                    *reinterpret_cast<float4 *>(par + p) = o;
+                    *reinterpret_cast<float4 *>(par + sw(lam + 1, p)) = o;
                     done = true;
                     } else {  // two adjacent node pairs per thread in 8-byte accesses
                         const int i = 2 * (loc ? wid * 32 + lane : tid);
                         const int ps = (i >> lam) << (lam + 1), j = i & (len - 1);
-                        const float2 x = *reinterpret_cast<const float2 *>(par + ps + j);
-                        const float2 y = *reinterpret_cast<const float2 *>(par + ps + len + j);
-                        const float2 gl = *reinterpret_cast<const float2 *>(cur + ps + j);
-                        const float2 gr = *reinterpret_cast<const float2 *>(cur + ps + len + j);
+                        const float2 x = *reinterpret_cast<const float2 *>(par + sw(lam + 1, ps + j));
+                        const float2 y = *reinterpret_cast<const float2 *>(par + sw(lam + 1, ps + len + j));
+                        const float2 gl = *reinterpret_cast<const float2 *>(cur + sw(lam, ps + j));
+                        const float2 gr = *reinterpret_cast<const float2 *>(cur + sw(lam, ps + len + j));
                         const uint32_t w = bx[(ps + j) >> 5] >> ((ps + j) & 31);
                         float2 ax, ay;
                         bwd_pair<T>(x.x, y.x, gl.x, gr.x, w & 1u, s, gs, ax.x, ay.x);
                         bwd_pair<T>(x.y, y.y, gl.y, gr.y, (w >> 1) & 1u, s, gs, ax.y, ay.y);
-                        *reinterpret_cast<float2 *>(par + ps + j) = ax;
-                        *reinterpret_cast<float2 *>(par + ps + len + j) = ay;
+                        *reinterpret_cast<float2 *>(par + sw(lam + 1, ps + j)) = ax;
+                        *reinterpret_cast<float2 *>(par + sw(lam + 1, ps + len + j)) = ay;
                         done = true;
                     }
                 }
