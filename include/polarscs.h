@@ -46,6 +46,9 @@ extern "C" {
 #define POLAR_CRC_FAIL 1 /* no complete path passed the CRC: the first complete
                             path popped is returned (Sec. 2.2.5, CRC rule) */
 #define POLAR_TIMEOUT 2  /* iteration guard tripped; never expected, output zero */
+#define POLAR_DEBUG_FAIL 4 /* bounds-checked debug builds only (POLAR_DEBUG): an
+                              internal index check failed in this frame; its
+                              output is not meaningful */
 
 /* errors */
 #define POLAR_EINVAL (-1) /* bad argument: N not a power of 2 in range, K not in

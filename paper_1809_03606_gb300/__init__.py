@@ -18,7 +18,7 @@ import numpy as np
 
 from . import _build
 
-POLAR_OK, POLAR_CRC_FAIL, POLAR_TIMEOUT = 0, 1, 2
+POLAR_OK, POLAR_CRC_FAIL, POLAR_TIMEOUT, POLAR_DEBUG_FAIL = 0, 1, 2, 4
 POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ELIMIT, POLAR_ESCRATCH, POLAR_ETIMEOUT = -1, -2, -3, -4, -5, -6
 MAX_N_GPU, MAX_D_GPU, MAX_L_GPU = 8192, 64, 255
 MAX_D_GPU_DEEP = 65536  # scs_decode_batch of min-sum plans (memory stack)

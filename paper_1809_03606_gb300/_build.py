@@ -40,20 +40,26 @@ def _deps() -> list[str]:
     return out
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
+def variant_lib(variant: str) -> str:
+    return LIB if not variant else os.path.join(BUILD, f"libpolarscs_{variant}.so")
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, variant: str = "") -> str:
-    """Build the library.  variant="timers" builds a separate debug library
-    (libpolarscs_timers.so) with the per-phase cycle counters compiled in."""
-    lib = LIB if not variant else os.path.join(BUILD, f"libpolarscs_{variant}.so")
-    defines = {"": [], "timers": ["-DPOLAR_PHASE_TIMERS"]}[variant]
-    if not force and not variant and not needs_build():
-        return LIB
+    """Build the library.  Variants are separate libraries for diagnosis:
+    "timers" (libpolarscs_timers.so) with the per-phase cycle counters
+    compiled in, "debug" (libpolarscs_debug.so) with the decoder's index
+    checks (POLAR_DEBUG: a failed check marks the frame POLAR_DEBUG_FAIL)."""
+    lib = variant_lib(variant)
+    defines = {"": [], "timers": ["-DPOLAR_PHASE_TIMERS"], "debug": ["-DPOLAR_DEBUG"]}[variant]
+    if not force and not needs_build(lib):
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 

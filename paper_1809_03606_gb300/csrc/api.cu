@@ -12,6 +12,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "plan.h"
 
 namespace polarscs {
@@ -30,6 +32,9 @@ void free_set_device(polar_plan_set *set);
 template <typename T>
 int launch_gsc(const polar_plan *p, const uint8_t *d_info_mask, const T *d_llr, const uint32_t *d_u, int B,
                const T *d_scales, T *d_loss, T *d_grad_scales, T *d_grad_llr, T *d_leaf, cudaStream_t stream);
+
+TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
 
 // Per-call scratch comes from the device's default stream-ordered pool.  By
 // default that pool returns memory to the driver at every synchronisation,
@@ -149,6 +154,7 @@ extern "C" int polar_plan_set_scales(polar_plan *p, const float *scales) {
 
 extern "C" int scs_decode_batch(const polar_plan *p, const float *d_llr, int B, int D, int L, uint32_t *d_info,
                                 float *d_pm, int8_t *d_status, uint32_t *d_stats, void *stream) {
+    TraceRange trace("scs_decode_batch");
     if (!p || B < 0 || D < 1 || L < 1) return POLAR_EINVAL;
     if (B > 0 && (!d_llr || !d_info || !d_pm || !d_status)) return POLAR_EINVAL;
     if (p->N > POLAR_MAX_N_GPU || D > POLAR_MAX_D_GPU_DEEP || L > POLAR_MAX_L_GPU) return POLAR_ELIMIT;
@@ -163,6 +169,7 @@ extern "C" int scs_decode_batch(const polar_plan *p, const float *d_llr, int B, 
 extern "C" int scs_decode_batch_noalloc(const polar_plan *p, const float *d_llr, int B, int D, int L,
                                         uint32_t *d_info, float *d_pm, int8_t *d_status, uint32_t *d_stats,
                                         void *stream) {
+    TraceRange trace("scs_decode_batch_noalloc");
     if (!p || B < 0 || D < 1 || L < 1) return POLAR_EINVAL;
     if (B > 0 && (!d_llr || !d_info || !d_pm || !d_status)) return POLAR_EINVAL;
     if (p->N > POLAR_MAX_N_GPU || D > POLAR_MAX_D_GPU || L > POLAR_MAX_L_GPU) return POLAR_ELIMIT;
@@ -209,6 +216,7 @@ extern "C" int scs_decode_mixed(const polar_plan_set *set, const int32_t *d_fram
                                 int Dmax, const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info,
                                 const int64_t *d_info_off, float *d_pm, int8_t *d_status, uint32_t *d_stats,
                                 void *stream) {
+    TraceRange trace("scs_decode_mixed");
     int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
     if (rc || B == 0) return rc;
     return launch_scs_decode_mixed(set, reinterpret_cast<const int4 *>(d_frames), d_order, B, Dmax, d_llr,
@@ -234,6 +242,7 @@ extern "C" int scs_decode_mixed_split(const polar_plan_set *set, const int32_t *
                                       int B, int n_two, int Dmax, const float *d_llr, const int64_t *d_llr_off,
                                       uint32_t *d_info, const int64_t *d_info_off, float *d_pm, int8_t *d_status,
                                       uint32_t *d_stats, void *stream) {
+    TraceRange trace("scs_decode_mixed_split");
     int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
     if (rc || B == 0) return rc;
     if (!d_order || n_two < 0 || n_two > B || (n_two > 0 && Dmax <= 32)) return POLAR_EINVAL;
@@ -279,6 +288,7 @@ extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, cons
                               const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info,
                               const int64_t *d_info_off, float *d_pm, int8_t *d_status, void *stream, int *wpb_out,
                               int *chunk_out) {
+    TraceRange trace("scs_tune_mixed");
     int rc = check_mixed(set, d_frames, B, Dmax, d_llr, d_llr_off, d_info, d_info_off, d_pm, d_status);
     if (rc) return rc;
     if (B == 0) return POLAR_EINVAL;
@@ -331,6 +341,7 @@ extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, cons
 template <typename T>
 static int gsc_call(const polar_plan *p, const T *d_llr, const uint32_t *d_u, int B, const T *d_scales, T *d_loss,
                     T *d_grad_scales, T *d_grad_llr, T *d_leaf, void *stream) {
+    TraceRange trace("gsc_loss");
     if (!p || B < 1 || !d_llr || !d_u || !d_scales || !d_loss) return POLAR_EINVAL;
     const DeviceTables *dt = nullptr;
     int rc = plan_device(p, &dt);
@@ -404,6 +415,7 @@ extern "C" int polar_mixed_split_order(const polar_plan_set *set, const int32_t 
 
 extern "C" int polar_encode_batch(const polar_plan *p, const uint32_t *d_msg, int B, uint32_t *d_codeword,
                                   void *stream) {
+    TraceRange trace("polar_encode_batch");
     if (!p || B < 0) return POLAR_EINVAL;
     if (B > 0 && (!d_msg || !d_codeword)) return POLAR_EINVAL;
     if (B == 0) return 0;
@@ -441,6 +453,7 @@ extern "C" int polar_encode(const uint8_t *msg, int N, int K, const uint8_t *fro
 
 extern "C" int scs_decode(const float *llr, int N, int K, const uint8_t *frozen, int D, int L, int crc,
                           uint8_t *info_out, float *pm_out) {
+    TraceRange trace("scs_decode");
     if (!llr || !frozen || !info_out || !pm_out) return POLAR_EINVAL;
     polar_plan *p = nullptr;
     int rc = polar_plan_create(N, K, frozen, 1, crc, &p);

@@ -92,6 +92,17 @@ struct polar_plan_set {
 
 namespace polarscs {
 
+// An NVTX range over the lifetime of the object (host side): every C ABI
+// entry point that launches work names itself, so a trace (nsys, ncu --nvtx)
+// shows which call issued which kernels.  Without an attached tool the calls
+// return at once.
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 int validate_code(int N, int K, const uint8_t *frozen, int crc);
 // CRC syndrome rows over codeword bits for the plan's encoding (needs
 // info_pos, crc_contrib).

@@ -128,6 +128,16 @@ __device__ unsigned long long g_phase_cycles[PH_N];
 #define PT_FLUSH
 #endif
 
+// POLAR_DEBUG builds check the indices of the shared-memory tree, the beta
+// array, the visit counters, the snapshots and the message positions before
+// they are used; a failed check skips the access and marks the frame, whose
+// status becomes POLAR_DEBUG_FAIL.  Other builds compile the checks away.
+#ifdef POLAR_DEBUG
+#define PCK(c) ((c) ? true : (bad = 1, false))
+#else
+#define PCK(c) true
+#endif
+
 __device__ __forceinline__ float f_minsum(float a, float b) {
     // Eq. minsum: sign(a) sign(b) min(|a|, |b|); the sign bit is the XOR of
     // the operands' sign bits
@@ -325,14 +335,21 @@ struct Warp {
     uint32_t *scr;    // global: (D + 1) snapshot slots
     const float *root;
     const float *scales;  // f output scale per stage, or null (plain min-sum)
+    mutable int bad;      // POLAR_DEBUG builds: an index check failed in this frame
 
     __device__ const float *stage(int lam) const { return lam == n ? root : alpha + (1 << lam); }
+    __device__ int N() const { return 1 << n; }
+    __device__ bool PCK_snap(int ss, int slam) const { return PCK(slam >= 0 && slam <= n && ss >= 0 && ss + (1 << slam) <= N()); }
 
     // alpha of the even child (lamc) from its parent (Eq. llrcalc, f); every
     // min-sum f output is multiplied by the stage scale (1.0, an exact
     // identity, for plain min-sum); EXACT: the box-plus f itself
     template <bool EXACT>
     __device__ void op_f(int lamc) const {
+        if (!PCK(lamc >= 0 && lamc < n)) {
+            __syncwarp();
+            return;
+        }
         const int len = 1 << lamc;
         float *C = alpha + len;
         const float sv = scales ? __ldg(scales + lamc) : 1.0f;
@@ -367,6 +384,10 @@ struct Warp {
     // alpha of the odd child (lamc, sc) from its parent and the left
     // sibling's bits beta[sc - 2^lamc, sc) (Eq. llrcalc, g)
     __device__ void op_g(int lamc, int sc) const {
+        if (!PCK(lamc >= 0 && lamc < n && sc >= (1 << lamc) && sc + (1 << lamc) <= N())) {
+            __syncwarp();
+            return;
+        }
         const int len = 1 << lamc;
         const int sl = sc - len;
         float *C = alpha + len;
@@ -403,6 +424,10 @@ struct Warp {
 
     // in-place beta operation of Sec. 4: beta[sl + i] ^= beta[sr + i]
     __device__ void op_comb(int lamc, int sr) const {
+        if (!PCK(lamc >= 0 && lamc < n && sr >= (1 << lamc) && sr + (1 << lamc) <= N())) {
+            __syncwarp();
+            return;
+        }
         const int len = 1 << lamc;
         const int sl = sr - len;
         if (len >= 32) {
@@ -420,6 +445,10 @@ struct Warp {
 
     // set beta[s, s + 2^lam) to all-zero or all-one
     __device__ void set_range(int lam, int s, uint32_t bit) const {
+        if (!PCK(lam >= 0 && lam <= n && s >= 0 && s + (1 << lam) <= N())) {
+            __syncwarp();
+            return;
+        }
         const int len = 1 << lam;
         if (len >= 32) {
             const uint32_t v = bit ? FULL : 0u;
@@ -436,6 +465,7 @@ struct Warp {
     // ---- reductions of the node decoders over the node's alpha ----
     // hard decisions into beta[s, s + 2^lam); returns their parity (XOR)
     __device__ uint32_t node_hd(int lam, int s) const {
+        if (!PCK(lam >= 0 && lam <= n && s >= 0 && s + (1 << lam) <= N())) return 0u;
         const int len = 1 << lam;
         const float *A = stage(lam);
         uint32_t par = 0;
@@ -461,6 +491,7 @@ struct Warp {
     // v[i] += v[i + h], h = 2^(lam-1) ... 1.  Levels wider than a warp are
     // written into the free alpha stages below the node.
     __device__ float node_sum(int lam, int mode) const {
+        if (!PCK(lam >= 0 && lam <= n)) return 0.0f;
         const int len = 1 << lam;
         const float *A = stage(lam);
         if (len <= 32) {
@@ -477,6 +508,10 @@ struct Warp {
     // REP node of at most 32 values: S = sum alpha, and the penalties of the
     // all-zero and all-one words, each summed in halving order in one tree
     __device__ void rep_sums(int lam, float &S, float &pen0, float &pen1) const {
+        if (!PCK(lam >= 0 && lam <= 5)) {
+            S = pen0 = pen1 = 0.0f;
+            return;
+        }
         const int len = 1 << lam;
         const float *A = stage(lam);
         const float x = lane < len ? A[lane] : 0.0f;
@@ -498,6 +533,7 @@ struct Warp {
 
     // the k least reliable positions (|alpha|, ties to the lower index)
     __device__ void node_least(int lam, int k, int *m, float *mag) const {
+        if (!PCK(lam >= 0 && lam <= n && k <= 4)) return;
         const int len = 1 << lam;
         const float *A = stage(lam);
         if (len > 32) {
@@ -525,6 +561,15 @@ struct Warp {
 
     // flip the candidate's positions relative to the node's hard decisions
     __device__ void apply_flips(uint32_t mask, const int *m, int s, int lam) const {
+#ifdef POLAR_DEBUG
+        bool in = lam >= 0 && lam <= n && s >= 0 && s + (1 << lam) <= N();
+        for (int j = 0; j < 4; ++j)
+            if ((mask >> j) & 1u) in = in && m[j] >= 0 && m[j] < (1 << lam);
+        if (!PCK(in)) {
+            __syncwarp();
+            return;
+        }
+#endif
         if (lam <= 5) {  // the node lies in one word: one masked XOR
             if (lane == 0 && mask) {
                 uint32_t x = (mask & FLIP_ALL) ? ((lam == 5) ? FULL : ((1u << (1 << lam)) - 1u)) : 0u;
@@ -608,7 +653,8 @@ __device__ __noinline__ bool crc_ok(const Code &c, const uint32_t *beta, int lan
 // output: re-encode the codeword estimate (F is an involution, Sec. 2.2.2)
 // and read the message bits off the information set; a systematic code
 // carries them in the codeword estimate itself
-__device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *orow, int lane) {
+__device__ __noinline__ int write_output(const Code &c, uint32_t *u, uint32_t *orow, int lane) {
+    int bad = 0;
     const int W = c.W, N = c.N;
     if (!c.systematic) {
         #pragma unroll 1
@@ -636,12 +682,13 @@ __device__ __noinline__ void write_output(const Code &c, uint32_t *u, uint32_t *
             const int j = ow * 32 + bb;
             if (j < c.Kmsg) {
                 const int p = __ldg(c.msg_pos + j);
-                word |= ((u[p >> 5] >> (p & 31)) & 1u) << bb;
+                if (PCK(p >= 0 && p < c.N)) word |= ((u[p >> 5] >> (p & 31)) & 1u) << bb;
             }
         }
         orow[ow] = word;
     }
     __syncwarp();
+    return bad;
 }
 
 // ---- stack and snapshot bookkeeping (plain inline functions: the stack
@@ -944,6 +991,9 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
     constexpr uint32_t nosnap = DEEP ? NOSNAP_DEEP : NOSNAP;
     constexpr int mask_shift = DEEP ? 24 : 8;
     const int lane = w.lane;
+#ifdef POLAR_DEBUG
+    int &bad = w.bad;  // the index checks of this function mark the frame
+#endif
     const int N = c.N, W = c.W, n = c.n;
     const int SW = c.snap_words;
     const int max_iter = L * (c.nbranch + 9) + 2;
@@ -1089,6 +1139,16 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             if (applied ^ p_mask) w.apply_flips(applied ^ p_mask, cm, cs, clam);
             applied = p_mask;
         } else {  // path switch (Sec. 3.3)
+#ifdef POLAR_DEBUG
+            {  // the snapshot's node must lie inside the code
+                const uint32_t *sp = w.scr + size_t(p_snap) * SW;
+                const int ss = int(sp[W + 2]), slam = int(sp[W + 3]);
+                if (!w.PCK_snap(ss, slam)) {
+                    status = POLAR_TIMEOUT;
+                    break;
+                }
+            }
+#endif
             switched = true;
             ++n_switch;
             ops += uint32_t(W);
@@ -1224,7 +1284,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             nbits = s + len;
             meta = uint32_t(s + len) | (uint32_t(t + 1) << 16);
             uint32_t vc = 0;
-            if (lane == 0) vc = ++w.cnt[op.w];
+            if (lane == 0 && PCK(int(op.w) < c.nbranch)) vc = ++w.cnt[op.w];
             vc = __shfl_sync(FULL, vc, 0);
             __syncwarp();
             if (int(vc) >= L) {
@@ -1330,9 +1390,14 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
     }
     __syncwarp();
     if (!c.systematic) ops += uint32_t(n) * uint32_t(W);
-    write_output(c, w.beta, orow, lane);
+    const int out_bad = write_output(c, w.beta, orow, lane);
+#ifdef POLAR_DEBUG
+    if (__any_sync(FULL, w.bad || out_bad)) status = POLAR_DEBUG_FAIL;
+#else
+    (void)out_bad;
+#endif
     if (lane == 0) {
-        if (status == POLAR_TIMEOUT) out_pm = __int_as_float(0x7f800000);
+        if (status == POLAR_TIMEOUT || status == POLAR_DEBUG_FAIL) out_pm = __int_as_float(0x7f800000);
         a.pm_out[b] = out_pm;
         a.status_out[b] = int8_t(status);
         if (STATS && a.stats_out) {  // without counters all counting is dead code
@@ -1377,7 +1442,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
             if constexpr (!MIXED) {
                 const Code &c = a.code;
                 Warp w{lane, c.n, a.llr_vec, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
-                       my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales};
+                       my + 4 * c.N + 4 * c.W, scr, a.llr + size_t(b) * c.N, c.scales, 0};
                 MemStack ms{nullptr, nullptr, 0};
                 if constexpr (NS == 0)
                     ms = MemStack{reinterpret_cast<uint4 *>(scr + a.deep_ent_off),
@@ -1395,7 +1460,7 @@ __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) 
                 const Code &c = codes_s[fd.x];
                 const long long lo = a.llr_off[b];
                 Warp w{lane, c.n, (a.llr_vec && (lo & 3) == 0) ? 1 : 0, reinterpret_cast<float *>(my),
-                       reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales};
+                       reinterpret_cast<uint32_t *>(my + 4 * c.N), my + 4 * c.N + 4 * c.W, scr, a.llr + lo, c.scales, 0};
                 decode_frame<NS, false, STATS>(a, c, fd.y, fd.z, w, b, a.info_out + a.info_off[b], MemStack{nullptr, nullptr, 0});
             }
         }
@@ -1467,7 +1532,7 @@ __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
             for (int i = lane; i < c.N; i += 32) stage[i] = __ldcg(src + i);
             __syncwarp();
             Warp w{lane, c.n, 1, reinterpret_cast<float *>(my), reinterpret_cast<uint32_t *>(my + 4 * c.N),
-                   my + 4 * c.N + 4 * c.W, scr, stage, c.scales};
+                   my + 4 * c.N + 4 * c.W, scr, stage, c.scales, 0};
             decode_frame<NS, false, false>(a, c, fd.y, fd.z, w, k, a.info_out + a.info_off[k], MemStack{nullptr, nullptr, 0});
         }
         if (lane == 0) {

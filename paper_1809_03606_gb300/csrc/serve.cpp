@@ -116,6 +116,7 @@ extern "C" int polar_serve(const polar_plan_set *set, const int32_t *req, const 
                            const float *pool_llr, const int64_t *pool_off, int P, int64_t arena_floats,
                            double wait_s, float *pm_out, int8_t *status_out, uint32_t *info_out,
                            const int64_t *info_off, double *latency_out, double *service_out, double *report) {
+    TraceRange trace("polar_serve");
     if (!set || !req || !arrival_s || R < 1 || !pool_llr || !pool_off || P < 1 || arena_floats < 1 || !pm_out ||
         !status_out || !latency_out || !report || wait_s <= 0.0)
         return POLAR_EINVAL;
@@ -360,6 +361,7 @@ extern "C" int polar_serve_baseline(const polar_plan_set *set, const int32_t *re
                                     const float *pool_llr, const int64_t *pool_off, int P, int64_t arena_floats,
                                     double interval_s, double wait_s, float *pm_out, int8_t *status_out,
                                     double *latency_out, double *report) {
+    TraceRange trace("polar_serve_baseline");
     if (!set || !req || !arrival_s || R < 1 || !pool_llr || !pool_off || P < 1 || arena_floats < 1 || !pm_out ||
         !status_out || !latency_out || !report || interval_s <= 0.0 || wait_s <= 0.0)
         return POLAR_EINVAL;
