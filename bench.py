@@ -403,6 +403,9 @@ def bench_ours(args, rank: int, world: int, local_rank: int, base=WORKLOAD) -> N
         del llrs, outs
         torch.cuda.empty_cache()
         mixed = measure_mixed(args, MIXED["frames"], rank, local_rank, steps=3, warmup=1, with_roofline=False)
+    subsystems = None
+    if base is WORKLOAD and world == 1 and not args.no_extras:
+        subsystems = measure_subsystems(args, rank, local_rank)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_frames, w)
@@ -429,6 +432,8 @@ def bench_ours(args, rank: int, world: int, local_rank: int, base=WORKLOAD) -> N
                 "clocks": clocks}
         if mixed is not None:
             line["mixed"] = mixed
+        if subsystems is not None:
+            line["subsystems"] = subsystems
         print(json.dumps(line), flush=True)
 
 
@@ -1013,6 +1018,124 @@ def bench_serve(args, rank: int, world: int, local_rank: int) -> None:
         print(json.dumps(line), flush=True)
 
 
+def measure_subsystems(args, rank: int, local_rank: int) -> dict:
+    """Compact measurements of the other workloads, for the default line: the
+    genie-aided SC gradient step (65,536 frames), one sweep of the paper's
+    decoder setting (7 x 2^19 frames, memory stack), and a short serving run
+    (1 s of 5 M req/s Poisson arrivals, the first 0.5 s through both engines
+    with identical outputs, and 1 s at 0.5 M req/s split into waiting and
+    service time)."""
+    import numpy as np
+    import torch
+
+    import paper_1809_03606_gb300 as ps
+    import workloads as W
+
+    out = {}
+    # genie-aided SC: forward + reverse with unit scales
+    g = dict(GSC)
+    N, K = g["N"], g["K"]
+    n = N.bit_length() - 1
+    plan = ps.Plan(N, K, ps.polar_construct(N, K, g["design_snr_db"]), fast_nodes=False)
+    llrs, _ = make_gpu_inputs(ps, plan, g["frames"], rank, g)
+    msg = W.message_bits(rank_seed(rank, g), g["frames"], K)
+    u = torch.from_numpy(ps.u_from_messages(plan, msg)).cuda()
+    ones = torch.ones(n, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        ps.gsc_loss_grad(plan, llrs[0], u, ones)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        ps.gsc_loss_grad(plan, llrs[0], u, ones)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    out["gsc"] = {"workload": f"{g['frames']} frames of PC({N},{K}) at 2.0 dB, forward + reverse, {n} stage scales",
+                  "ms_per_step": ms, "frames_per_s": g["frames"] / (ms / 1e3)}
+    del llrs, u
+    torch.cuda.empty_cache()
+
+    # the paper's decoder setting: one warm-up and two timed sweeps
+    w = dict(PAPER)
+    fr = ps.polar_construct(w["N"], w["K"], w["design_snr_db"])
+    plan = ps.Plan(w["N"], w["K"], fr, fast_nodes=w["fast"], crc=w["crc"], systematic=w["systematic"])
+    llrs, d_msg = make_gpu_inputs(ps, plan, w["frames"], rank, w)
+    B = w["frames"]
+    res = [(torch.empty((B, plan.msg_words), dtype=torch.int32, device="cuda"),
+            torch.empty(B, dtype=torch.float32, device="cuda"), torch.empty(B, dtype=torch.int8, device="cuda"))
+           for _ in llrs]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in llrs]
+    for rep in range(3):
+        for p_, x in enumerate(llrs):
+            if rep:
+                ev[p_][0].record()
+            ps.scs_decode_batch(plan, x, w["D"], w["L"], *res[p_])
+            if rep:
+                ev[p_][1].record()
+        torch.cuda.synchronize()
+        if rep == 1:
+            ms1 = [e[0].elapsed_time(e[1]) for e in ev]
+    ms2 = [e[0].elapsed_time(e[1]) for e in ev]
+    pt_ms = [min(a, b) for a, b in zip(ms1, ms2)]
+    kmsg = w["K"] - w["crc"]
+    fer = [float((r[0] != d_msg).any(dim=1).double().mean().item()) for r in res]
+    out["paper"] = {"workload": workload_name(w), "info_gbps": len(llrs) * B * kmsg / (sum(pt_ms) / 1e3) / 1e9,
+                    "ms_per_sweep": sum(pt_ms),
+                    "per_point": [{"ebn0_db": e, "ms": t, "info_gbps": B * kmsg / (t / 1e3) / 1e9, "fer": f}
+                                  for e, t, f in zip(w["ebn0"], pt_ms, fer)]}
+    del llrs, res, d_msg
+    torch.cuda.empty_cache()
+
+    # serving: continuous batching against one size per launch on the same stream
+    m = make_mixed_inputs(ps, SERVE["pool"], rank, dict(MIXED, seed=SERVE["seed"]))
+    pool = m["llr"].cpu().numpy()
+    pset = ps.PlanSet(m["plans"])
+    P = SERVE["pool"]
+    kmsg_pool = (m["Ks"] - MIXED["crc"]).astype(np.int64)
+    arena = SERVE["arena_bytes"] // 4
+
+    def stream(rate_hz, dur, seed):
+        arr = W.poisson_arrivals(seed, rate_hz, dur)
+        p_ = np.arange(arr.size) % P
+        req = np.stack([m["idx"][p_], m["D"][p_], m["D"][p_], p_], axis=1).astype(np.int32)
+        return req, arr, p_
+
+    def summary(o, p_):
+        lat = o["latency"]
+        ok = np.isfinite(lat)
+        t_end = o["report"]["seconds_to_last_completion"]
+        r = {"requests": int(lat.size), "completed": int(ok.sum()),
+             "throughput_req_s": float(ok.sum()) / t_end if t_end > 0 else None,
+             "info_gbps": float(kmsg_pool[p_[ok]].sum()) / t_end / 1e9 if t_end > 0 else None,
+             "p50_ms": float(np.percentile(lat[ok], 50) * 1e3), "p99_ms": float(np.percentile(lat[ok], 99) * 1e3)}
+        svc = o.get("service")
+        if svc is not None:
+            r["p99_service_ms"] = float(np.percentile(svc[ok], 99) * 1e3)
+            r["p99_wait_ms"] = float(np.percentile((lat - svc)[ok], 99) * 1e3)
+        return r
+
+    req, arr, p_ = stream(SERVE["rate"], 1.0, SERVE["seed"])
+    full = ps.polar_serve(pset, req, arr, pool, m["llr_off"], arena, wait_s=60.0)
+    cut = int(np.searchsorted(arr, SERVE["compare_seconds"]))
+    sp = ps.polar_serve(pset, req[:cut], arr[:cut], pool, m["llr_off"], arena, wait_s=60.0)
+    bp = ps.polar_serve_baseline(pset, req[:cut], arr[:cut], pool, m["llr_off"], arena,
+                                 interval_s=SERVE["interval_s"], wait_s=600.0)
+    same = bool(np.array_equal(sp["pm"].view(np.uint32), bp["pm"].view(np.uint32)) and
+                np.array_equal(sp["status"], bp["status"]))
+    lreq, larr, lp = stream(5e5, 1.0, SERVE["seed"] + 7)
+    low = ps.polar_serve(pset, lreq, larr, pool, m["llr_off"], arena, wait_s=60.0)
+    out["serving"] = {"workload": "Poisson arrivals from the mixed mix (pool of 262,144 frames cycled)",
+                      "offered_5M_req_s_for_1s": summary(full, p_),
+                      "prefix_0.5s": {"continuous_batching": summary(sp, p_[:cut]),
+                                      "one_size_per_launch": summary(bp, p_[:cut]), "identical_outputs": same},
+                      "offered_0.5M_req_s_for_1s": summary(low, lp),
+                      "rc": [int(full["rc"]), int(sp["rc"]), int(bp["rc"]), int(low["rc"])]}
+    del m, pool
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(frames: int, w=WORKLOAD):
     import os as _os
 
@@ -1046,6 +1169,8 @@ def main(argv=None) -> int:
     ap.add_argument("--no-lpt", action="store_true", help="mixed workload: claim frames in batch order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="sweep: skip the mixed-batch comparison object")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="sweep: skip the compact gradient, paper-setting and serving measurements")
     ap.add_argument("--systematic", action="store_true", help="sweep: systematic encoding and decoding")
     args = ap.parse_args(argv)
     if args.warmup < 3:
