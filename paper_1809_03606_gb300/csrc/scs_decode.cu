@@ -68,7 +68,12 @@ struct Code {
     int systematic;  // message bits read straight from the codeword estimate
 };
 
-constexpr int kMaxCodes = 64;  // codes of one mixed batch (shared-memory table)
+// bytes of a plan set's code table (at most 64 codes) at the front of a mixed
+// or served launch's dynamic shared memory: sized by the set's codes, not by
+// the largest set, so that a set of large codes keeps one more block per SM
+// (e.g. 25 codes up to N = 2048: 6 blocks of 4 warps fit, against 5 with a
+// 64-entry table)
+int codes_smem_bytes(int ncodes) { return (int(sizeof(Code)) * ncodes + 15) & ~15; }
 // scratch budget of one memory-stack launch (D > 64): fewer resident warps
 // when one warp's snapshots and entries are large
 constexpr long long kDeepScratchBytes = 8LL << 30;
@@ -95,6 +100,7 @@ struct Args {
     long long scratch_stride;   // snapshot words per warp
     unsigned *counter;
     int warp_smem;              // bytes of shared memory per warp
+    int codes_smem;             // mixed / served: bytes of the code table before the warps' areas
     int llr_vec;                // the LLR buffer is 16-byte aligned
     int chunk;                  // frames claimed per atomic
     // served mode: requests become decodable when the host publishes them
@@ -1420,14 +1426,14 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
 template <bool MIXED, int NS, bool EXACT, bool STATS>
 __global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Code codes_s[MIXED ? kMaxCodes : 1];
+    Code *codes_s = reinterpret_cast<Code *>(smem);  // mixed: the set's codes (a.codes_smem bytes)
     if (MIXED) {
         for (int i = threadIdx.x; i < a.ncodes; i += blockDim.x) codes_s[i] = a.codes[i];
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    unsigned char *my = smem + size_t(wib) * a.warp_smem;
+    unsigned char *my = smem + a.codes_smem + size_t(wib) * a.warp_smem;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
     uint32_t *scr = a.scratch + size_t(gwarp) * size_t(a.scratch_stride);
     for (;;) {
@@ -1486,12 +1492,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 template <int NS>
 __global__ void __launch_bounds__(128, 6) scs_serve_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Code codes_s[kMaxCodes];
+    Code *codes_s = reinterpret_cast<Code *>(smem);  // the set's codes (a.codes_smem bytes)
     for (int i = threadIdx.x; i < a.ncodes; i += blockDim.x) codes_s[i] = a.codes[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    unsigned char *my = smem + size_t(wib) * a.warp_smem;
+    unsigned char *my = smem + a.codes_smem + size_t(wib) * a.warp_smem;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
     uint32_t *scr = a.scratch + size_t(gwarp) * size_t(a.scratch_stride);
     for (;;) {
@@ -1593,8 +1599,9 @@ const void *mixed_kernel(int Dmax, bool stats) {
     return stats ? kernel_fn<true, 1, false, true>() : kernel_fn<true, 1, false, false>();
 }
 
-// block size and persistent grid for kernel `fn` with `warp_smem` bytes per warp
-int launch_shape(const void *fn, bool mixed, int warp_smem, int B, int wpb, int *grid_out, int *wpb_out,
+// block size and persistent grid for kernel `fn` with `warp_smem` bytes per
+// warp after `table_smem` bytes per block (the code table of a mixed launch)
+int launch_shape(const void *fn, int table_smem, int warp_smem, int B, int wpb, int *grid_out, int *wpb_out,
                  int *smem_out) {
     int dev = 0, sms = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1602,10 +1609,9 @@ int launch_shape(const void *fn, bool mixed, int warp_smem, int B, int wpb, int 
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int static_smem = mixed ? int(sizeof(Code)) * kMaxCodes : int(sizeof(Code));
-    while (wpb > 1 && wpb * warp_smem + static_smem > max_smem) wpb >>= 1;
-    if (wpb * warp_smem + static_smem > max_smem) return POLAR_ELIMIT;
-    const int smem = wpb * warp_smem;
+    while (wpb > 1 && table_smem + wpb * warp_smem > max_smem) wpb >>= 1;
+    if (table_smem + wpb * warp_smem > max_smem) return POLAR_ELIMIT;
+    const int smem = table_smem + wpb * warp_smem;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 0;
@@ -1664,7 +1670,7 @@ int launch_scs_decode(const polar_plan *p, const DeviceTables *dt, const float *
 
     int grid = 0, wpb = 0, smem = 0;
     const void *fn = uniform_kernel(p, D, d_stats != nullptr);
-    int rc = launch_shape(fn, false, a.warp_smem, B, wpb_pref, &grid, &wpb, &smem);
+    int rc = launch_shape(fn, 0, a.warp_smem, B, wpb_pref, &grid, &wpb, &smem);
     if (rc) return rc;
     if (deep_fit > 0 && (long long)grid * wpb > deep_fit) grid = int(deep_fit / wpb);
     int dev = 0;
@@ -1768,6 +1774,7 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     a.status_out = d_status;
     a.stats_out = d_stats;
     a.warp_smem = warp_smem_bytes(set->Nmax, set->Wmax, set->nbranch_max);
+    a.codes_smem = codes_smem_bytes(a.ncodes);
     a.llr_vec = ((reinterpret_cast<uintptr_t>(d_llr) & 15u) == 0u) ? 1 : 0;
     a.chunk = chunk;
     a.scratch_stride = (long long)(Dmax + 1) * (((set->Wmax + 4) + 7) & ~7);
@@ -1775,7 +1782,7 @@ int launch_scs_decode_mixed(const polar_plan_set *set, const int4 *d_frames, con
     int grid = 0, wpb = 0, smem = 0;
     const int nb_units = (B + chunk - 1) / chunk;
     const void *fn = mixed_kernel(Dmax, d_stats != nullptr);
-    int rc = launch_shape(fn, true, a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem);
+    int rc = launch_shape(fn, a.codes_smem, a.warp_smem, nb_units, wpb_pref, &grid, &wpb, &smem);
     if (rc) return rc;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1828,6 +1835,7 @@ int launch_scs_serve(const polar_plan_set *set, const void *codes_v, const int4 
     a.pm_out = d_pm;
     a.status_out = d_status;
     a.warp_smem = warp_smem_bytes(set->Nmax, set->Wmax, set->nbranch_max);
+    a.codes_smem = codes_smem_bytes(a.ncodes);
     a.llr_vec = 1;  // requests are decoded from 16-byte aligned staging copies
     a.chunk = 1;
     a.serve_stage_off = (long long)(Dmax + 1) * (((set->Wmax + 4) + 7) & ~7);
@@ -1847,9 +1855,9 @@ int launch_scs_serve(const polar_plan_set *set, const void *codes_v, const int4 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int wpb = wpb_pref > 0 ? wpb_pref : 4;
-    const int static_smem = int(sizeof(Code)) * kMaxCodes;
-    while (wpb > 1 && wpb * a.warp_smem + static_smem > max_smem) wpb >>= 1;
-    const int smem = wpb * a.warp_smem;
+    while (wpb > 1 && a.codes_smem + wpb * a.warp_smem > max_smem) wpb >>= 1;
+    if (a.codes_smem + wpb * a.warp_smem > max_smem) return POLAR_ELIMIT;
+    const int smem = a.codes_smem + wpb * a.warp_smem;
     const void *kern = Dmax <= 32 ? reinterpret_cast<const void *>(scs_serve_kernel<1>)
                                   : reinterpret_cast<const void *>(scs_serve_kernel<2>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1994,7 +2002,7 @@ int launch_scs_decode_noalloc(const polar_plan *p, const float *d_llr, int B, in
     while (wpb > 1 && size_t(wpb) > warps_fit) wpb >>= 1;
     int grid = 0, smem = 0;
     const void *fn = uniform_kernel(p, D, d_stats != nullptr);
-    rc = launch_shape(fn, false, a.warp_smem, B, wpb, &grid, &wpb, &smem);
+    rc = launch_shape(fn, 0, a.warp_smem, B, wpb, &grid, &wpb, &smem);
     if (rc) return rc;
     const long long fit = (long long)(warps_fit / size_t(wpb));
     if (fit < grid) grid = int(fit);
