@@ -1423,8 +1423,15 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
 // MIXED = false: every frame uses a.code, a.D, a.L and row b of the LLR and
 // message buffers.  MIXED = true: frame b has its own code, D and L
 // (a.frames[b]) and offsets into packed LLR and message buffers.
+// Blocks per SM (registers per thread): measured per instantiation.  The
+// one-row min-sum decoder runs fastest at 9 (56 registers; 8: 1.3 % slower,
+// 7: 6 %, 10: 19 %); the memory stack at 8 (9: 11 % slower, 7: 7 %); the mixed
+// decoders at 6, which their shared memory allows for codes up to N = 2048.
+template <bool MIXED, int NS, bool EXACT>
+constexpr int decode_blocks_per_sm() { return MIXED ? 6 : ((NS == 1 && !EXACT) ? 9 : 8); }
+
 template <bool MIXED, int NS, bool EXACT, bool STATS>
-__global__ void __launch_bounds__(128, MIXED ? 6 : 8) scs_decode_kernel(Args a) {
+__global__ void __launch_bounds__(128, decode_blocks_per_sm<MIXED, NS, EXACT>()) scs_decode_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
     Code *codes_s = reinterpret_cast<Code *>(smem);  // mixed: the set's codes (a.codes_smem bytes)
     if (MIXED) {
