@@ -276,3 +276,47 @@ def test_split_launches_equal_one_launch_and_oracle(lib, oracle_lib):
         torch.cuda.synchronize()
         for r, x in zip(r1, (one.info, one.pm, one.status)):
             assert torch.equal(r, x)
+
+
+@pytest.mark.gpu
+def test_full_code_table_and_largest_code(lib, oracle_lib):
+    """A set of 64 codes, the most a set holds, one of them N = 8192: the code
+    table and the largest warp areas share the block's shared memory.  Every
+    frame equals its solo decode, in one launch and split by stack rows; a
+    sample also equals the oracle."""
+    torch = pytest.importorskip("torch")
+    codes = []
+    for N in (16, 32, 64, 128, 256, 512, 1024):
+        for r in (1 / 8, 1 / 4, 1 / 3, 3 / 8, 1 / 2, 5 / 8, 2 / 3, 3 / 4, 7 / 8):
+            K = max(1, round(N * r))
+            codes.append((N, K, 8 if K > 16 else 0))
+    codes.append((8192, 4096, 16))
+    assert len(codes) == 64
+    plans, frozens, idx, D, L, rows, msgs = _mixed_problem(oracle_lib, codes, 640, seed=41, ebn0_lo=2.5)
+    pset = ps.PlanSet(plans)
+    mb = ps.MixedBatch(pset, idx, D, L, rows)
+    mb.decode(pset)
+    torch.cuda.synchronize()
+    ref = (mb.info.clone(), mb.pm.clone(), mb.status.clone())
+    pm, st = mb.pm.cpu().numpy(), mb.status.cpu().numpy()
+    assert (idx == 63).sum() > 0
+    groups = {}
+    for b in range(mb.B):
+        groups.setdefault((int(idx[b]), int(D[b]), int(L[b])), []).append(b)
+    for (ci, d, l), bs in groups.items():
+        info_s, pm_s, st_s, _ = _solo(torch, plans[ci], [rows[b] for b in bs], d, l)
+        for j, b in enumerate(bs):
+            assert np.array_equal(mb.message_words(b), info_s[j]), b
+            assert pm[b].view(np.uint32) == pm_s[j].view(np.uint32) and st[b] == st_s[j], b
+    mb.info.zero_()
+    mb.pm.zero_()
+    mb.decode_split(pset)
+    torch.cuda.synchronize()
+    for r, g in zip(ref, (mb.info, mb.pm, mb.status)):
+        assert torch.equal(r, g)
+    for b in list(range(0, mb.B, 20)) + [int(np.nonzero(idx == 63)[0][0])]:
+        N, K, crc = codes[idx[b]]
+        st_o, m_o, pm_o, _, _ = oracle_lib.scs_decode(rows[b], N, K, frozens[idx[b]], fast=True, D=int(D[b]),
+                                                      L=int(L[b]), crc_len=crc)
+        got = ps.unpack_bits(mb.message_words(b)[None, :], K - crc)[0]
+        assert np.array_equal(got, m_o) and pm[b].view(np.uint32) == pm_o.view(np.uint32) and st[b] == st_o, b
