@@ -211,6 +211,18 @@ __device__ __noinline__ float node_sum_wide(float *alpha, const float *A, int le
     return __shfl_sync(FULL, v, 0);
 }
 
+// Loads of the channel LLRs and of beta snapshots: through L2 only (CG) or
+// the default path through L1.  A frame's LLR row and its snapshots are read
+// again, if at all, long after L1 has dropped them, so the register-stack
+// decoders load them through L2 and keep L1 for their spilled registers
+// (sweep +1.1 %, mixed batch +3 %); the memory-stack decoder measured 4 %
+// slower that way and keeps the default path.
+template <bool CG, class T>
+__device__ __forceinline__ T ld_l2(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // path switch: the popped path's beta from its snapshot (the node's hard
 // decisions) with its flips applied; returns the first bit position where
 // it may differ from the beta it replaces (out of line)
@@ -221,6 +233,45 @@ __device__ __noinline__ int restore_switch(const uint32_t *sp, uint32_t *beta, i
     #pragma unroll 1
     for (int k = lane; k < W; k += 32) {
         const uint32_t nv = sp[k];
+        const uint32_t x = nv ^ beta[k];
+        beta[k] = nv;
+        if (x && dl == EMPTY) dl = uint32_t(32 * k + __ffs(x) - 1);
+    }
+    dl = __reduce_min_sync(FULL, dl);
+    __syncwarp();
+    if (mask & FLIP_ALL) {
+        const int len = 1 << slam;
+        if (len >= 32) {
+            #pragma unroll 1
+            for (int k = lane; k < (len >> 5); k += 32) beta[(ss >> 5) + k] ^= FULL;
+        } else if (lane == 0) {
+            beta[ss >> 5] ^= ((1u << len) - 1u) << (ss & 31);
+        }
+    }
+    if (lane == 0) {
+        const int mm[4] = {int(m01 & 0xFFFFu), int(m01 >> 16), int(m23 & 0xFFFFu), int(m23 >> 16)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((mask >> j) & 1u) {
+                const int pos = ss + mm[j];
+                beta[pos >> 5] ^= 1u << (pos & 31);
+            }
+    }
+    __syncwarp();
+    return int(min(dl, uint32_t(ss)));  // the flips only touch [ss, ...)
+}
+
+// restore_switch, f_root and g_root with their global loads through L2 only
+// (the register-stack decoders).  Separate copies: with one template body
+// shared by both forms the memory-stack decoder, which runs the originals,
+// measured 2.6 % slower with the same registers and no spills.
+__device__ __noinline__ int restore_switch_cg(const uint32_t *sp, uint32_t *beta, int W, uint32_t mask, int lane) {
+    const uint32_t m01 = __ldcg(sp + W), m23 = __ldcg(sp + W + 1);
+    const int ss = int(__ldcg(sp + W + 2)), slam = int(__ldcg(sp + W + 3));
+    uint32_t dl = EMPTY;
+    #pragma unroll 1
+    for (int k = lane; k < W; k += 32) {
+        const uint32_t nv = __ldcg(sp + k);
         const uint32_t x = nv ^ beta[k];
         beta[k] = nv;
         if (x && dl == EMPTY) dl = uint32_t(32 * k + __ffs(x) - 1);
@@ -299,6 +350,54 @@ __device__ __noinline__ void g_root(const float *P, float *C, const uint32_t *be
     }
 }
 
+__device__ __noinline__ void f_root_cg(const float *P, float *C, int len, float sv, int vec, int exact, int lane) {
+    if (exact) {
+        #pragma unroll 1
+        for (int i = lane; i < len; i += 32) C[i] = f_exact(__ldcg(P + i), __ldcg(P + i + len));
+    } else if (vec && len >= 128) {
+        #pragma unroll 1
+        for (int i = 4 * lane; i < len; i += 128) {
+            const float4 x = __ldcg(reinterpret_cast<const float4 *>(P + i));
+            const float4 y = __ldcg(reinterpret_cast<const float4 *>(P + i + len));
+            float4 r;
+            r.x = __fmul_rn(sv, f_minsum(x.x, y.x));
+            r.y = __fmul_rn(sv, f_minsum(x.y, y.y));
+            r.z = __fmul_rn(sv, f_minsum(x.z, y.z));
+            r.w = __fmul_rn(sv, f_minsum(x.w, y.w));
+            *reinterpret_cast<float4 *>(C + i) = r;
+        }
+    } else {
+        #pragma unroll 1
+        for (int i = lane; i < len; i += 32) C[i] = __fmul_rn(sv, f_minsum(__ldcg(P + i), __ldcg(P + i + len)));
+    }
+}
+
+__device__ __noinline__ void g_root_cg(const float *P, float *C, const uint32_t *beta, int len, int sl, int vec,
+                                       int lane) {
+    if (vec && len >= 128) {
+        #pragma unroll 1
+        for (int i = 4 * lane; i < len; i += 128) {
+            const int pos = sl + i;
+            const uint32_t bits = beta[pos >> 5] >> (pos & 31);
+            const float4 x = __ldcg(reinterpret_cast<const float4 *>(P + i));
+            const float4 y = __ldcg(reinterpret_cast<const float4 *>(P + i + len));
+            float4 r;
+            r.x = g_op(x.x, y.x, bits & 1u);
+            r.y = g_op(x.y, y.y, (bits >> 1) & 1u);
+            r.z = g_op(x.z, y.z, (bits >> 2) & 1u);
+            r.w = g_op(x.w, y.w, (bits >> 3) & 1u);
+            *reinterpret_cast<float4 *>(C + i) = r;
+        }
+    } else {
+        #pragma unroll 1
+        for (int i = lane; i < len; i += 32) {
+            const int pos = sl + i;
+            const uint32_t bit = (beta[pos >> 5] >> (pos & 31)) & 1u;
+            C[i] = g_op(__ldcg(P + i), __ldcg(P + i + len), bit);
+        }
+    }
+}
+
 struct Least {
     int m[4];
     float mag[4];
@@ -350,7 +449,7 @@ struct Warp {
     // alpha of the even child (lamc) from its parent (Eq. llrcalc, f); every
     // min-sum f output is multiplied by the stage scale (1.0, an exact
     // identity, for plain min-sum); EXACT: the box-plus f itself
-    template <bool EXACT>
+    template <bool EXACT, bool CG>
     __device__ void op_f(int lamc) const {
         if (!PCK(lamc >= 0 && lamc < n)) {
             __syncwarp();
@@ -360,7 +459,7 @@ struct Warp {
         float *C = alpha + len;
         const float sv = scales ? __ldg(scales + lamc) : 1.0f;
         if (lamc + 1 == n) {
-            f_root(root, C, len, sv, llr_vec, EXACT ? 1 : 0, lane);
+            (CG ? f_root_cg : f_root)(root, C, len, sv, llr_vec, EXACT ? 1 : 0, lane);
             __syncwarp();
             return;
         }
@@ -389,6 +488,7 @@ struct Warp {
 
     // alpha of the odd child (lamc, sc) from its parent and the left
     // sibling's bits beta[sc - 2^lamc, sc) (Eq. llrcalc, g)
+    template <bool CG>
     __device__ void op_g(int lamc, int sc) const {
         if (!PCK(lamc >= 0 && lamc < n && sc >= (1 << lamc) && sc + (1 << lamc) <= N())) {
             __syncwarp();
@@ -398,7 +498,7 @@ struct Warp {
         const int sl = sc - len;
         float *C = alpha + len;
         if (lamc + 1 == n) {
-            g_root(root, C, beta, len, sl, llr_vec, lane);
+            (CG ? g_root_cg : g_root)(root, C, beta, len, sl, llr_vec, lane);
             __syncwarp();
             return;
         }
@@ -994,6 +1094,7 @@ template <int NS, bool EXACT, bool STATS>
 __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const int D, const int L, Warp &w,
                                              unsigned b, uint32_t *orow, const MemStack ms) {
     constexpr bool DEEP = NS == 0;
+    constexpr bool CG = !DEEP;  // LLR and snapshot loads through L2 only
     constexpr uint32_t nosnap = DEEP ? NOSNAP_DEEP : NOSNAP;
     constexpr int mask_shift = DEEP ? 24 : 8;
     const int lane = w.lane;
@@ -1136,7 +1237,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             if (beta_dirty) {
                 const uint32_t *sp = w.scr + size_t(cur_snap) * SW;
                 #pragma unroll 1
-                for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
+                for (int k = lane; k < W; k += 32) w.beta[k] = ld_l2<CG>(sp + k);
                 __syncwarp();
                 applied = 0u;
                 beta_dirty = false;
@@ -1158,7 +1259,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             switched = true;
             ++n_switch;
             ops += uint32_t(W);
-            div = restore_switch(w.scr + size_t(p_snap) * SW, w.beta, W, p_mask, lane);
+            div = (CG ? restore_switch_cg : restore_switch)(w.scr + size_t(p_snap) * SW, w.beta, W, p_mask, lane);
             beta_dirty = true;
         }
         PT(PH_BETA)
@@ -1247,8 +1348,8 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
             if (code <= OP_G) {  // an F or G, then run - 1 F ops down the left edge
                 #pragma unroll 1
                 for (int i = 0; i < run; ++i) {
-                    if (i == 0 && code == OP_G) w.op_g(lam, s);
-                    else w.template op_f<EXACT>(lam - i);
+                    if (i == 0 && code == OP_G) w.template op_g<CG>(lam, s);
+                    else w.template op_f<EXACT, CG>(lam - i);
                     if (sched) ops += 2u << (lam - i);
                 }
                 PT(PH_FG)
@@ -1389,7 +1490,7 @@ __device__ __forceinline__ void decode_frame(const Args &a, const Code &c, const
     if (out_src == 2) {
         const uint32_t *sp = w.scr + size_t(first_slot) * SW;
         #pragma unroll 1
-        for (int k = lane; k < W; k += 32) w.beta[k] = sp[k];
+        for (int k = lane; k < W; k += 32) w.beta[k] = ld_l2<CG>(sp + k);
     } else if (out_src == 0) {
         #pragma unroll 1
         for (int k = lane; k < W; k += 32) w.beta[k] = 0u;
