@@ -284,6 +284,19 @@ int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, const int32_t *
                    const float *d_llr, const int64_t *d_llr_off, uint32_t *d_info, const int64_t *d_info_off,
                    float *d_pm, int8_t *d_status, void *stream, int *wpb_out, int *chunk_out);
 
+/* The launch shape scs_decode_mixed and scs_decode_mixed_split use for the
+ * set, as scs_tune_mixed leaves it: warps_per_block in {1, 2, 4} and
+ * frames_per_claim in 1 .. 1024, or both 0 for the defaults (4 warps, 1
+ * frame).  For restoring a tuning result saved earlier instead of timing
+ * again (the paper has no counterpart; the binding keeps such results in a
+ * JSON file keyed by GPU and codes).  Host only, no device work; thread-safe.
+ * Errors: POLAR_EINVAL (null set, values out of range). */
+int polar_plan_set_tuning(polar_plan_set *set, int warps_per_block, int frames_per_claim);
+
+/* The set's current launch shape (0, 0 when it was never tuned or set).
+ * Host only.  Errors: POLAR_EINVAL (a null argument). */
+int polar_plan_set_get_tuning(const polar_plan_set *set, int *warps_per_block, int *frames_per_claim);
+
 /* ---- Genie-aided SC with per-stage min-sum scales (differentiation) ----
  * Built on Eq. minsum and Eq. llrcalc: with the transmitted bits known, every
  * g uses the true partial sums, and the f output written at stage lambda is

@@ -30,7 +30,7 @@ EXPORTED = (
     "polar_plan_set_create", "polar_plan_set_destroy", "scs_decode_mixed", "scs_tune_mixed",
     "gsc_loss", "gsc_loss_grad", "gsc_loss_f64", "gsc_loss_grad_f64", "polar_plan_set_scales", "polar_mixed_order",
     "polar_serve", "polar_serve_baseline", "polar_plan_set_systematic", "polar_plan_set_exact",
-    "polar_mixed_split_order", "scs_decode_mixed_split",
+    "polar_mixed_split_order", "scs_decode_mixed_split", "polar_plan_set_tuning", "polar_plan_set_get_tuning",
 )
 
 _lock = threading.Lock()
@@ -81,6 +81,8 @@ def load(build_if_missing: bool = False):
         lib.polar_plan_set_destroy.restype = None
         lib.scs_decode_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.scs_tune_mixed.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.polar_plan_set_tuning.argtypes = [vp, i32, i32]
+        lib.polar_plan_set_get_tuning.argtypes = [vp, vp, vp]
         lib.polar_mixed_order.argtypes = [vp, vp, i32, vp]
         lib.polar_mixed_split_order.argtypes = [vp, vp, i32, vp, vp]
         lib.scs_decode_mixed_split.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -342,6 +344,113 @@ def scs_tune_mixed(pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_of
         *_mixed_args(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status, order), _stream_ptr(stream),
         C.byref(w), C.byref(c)))
     return w.value, c.value
+
+
+def polar_plan_set_tuning(pset: PlanSet, warps_per_block: int, frames_per_claim: int) -> None:
+    """Set the set's mixed-batch launch shape (both 0: the defaults)."""
+    _check("polar_plan_set_tuning", load().polar_plan_set_tuning(pset.handle, int(warps_per_block),
+                                                                 int(frames_per_claim)))
+
+
+def polar_plan_set_get_tuning(pset: PlanSet):
+    """The set's mixed-batch launch shape: (warps per block, frames per claim), (0, 0) if unset."""
+    w, c = C.c_int(0), C.c_int(0)
+    _check("polar_plan_set_get_tuning", load().polar_plan_set_get_tuning(pset.handle, C.byref(w), C.byref(c)))
+    return w.value, c.value
+
+
+def tuning_key(pset: PlanSet, Dmax: int, device: str) -> str:
+    """Key of a tuning result: the GPU, the largest D and, per code, N, K, CRC
+    length, fast nodes, systematic form and a digest of the frozen set."""
+    import hashlib
+
+    codes = []
+    for pl in pset.plans:
+        fz = hashlib.sha256(np.ascontiguousarray(pl.frozen, dtype=np.uint8).tobytes()).hexdigest()[:12]
+        codes.append(f"{pl.N}/{pl.K}/{pl.crc}/{int(pl.fast)}/{int(pl.systematic)}/{fz}")
+    return f"{device}|D{int(Dmax)}|" + ";".join(codes)
+
+
+class TuningCache:
+    """Autotuner results kept in a JSON file between runs, so that a process
+    restores the launch shape of a known (GPU, codes, D) instead of timing
+    the nine shapes again.  The file maps tuning_key() to [warps per block,
+    frames per claim]; it is rewritten whole (through a temporary file) on
+    every store."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def _read(self) -> dict:
+        import json
+
+        try:
+            with open(self.path) as f:
+                data = json.load(f)
+        except FileNotFoundError:
+            return {}
+        if not isinstance(data, dict):
+            raise ValueError(f"{self.path}: not a tuning cache")
+        return data
+
+    def lookup(self, key: str):
+        v = self._read().get(key)
+        return None if v is None else (int(v[0]), int(v[1]))
+
+    def store(self, key: str, warps_per_block: int, frames_per_claim: int) -> None:
+        import json
+
+        data = self._read()
+        data[key] = [int(warps_per_block), int(frames_per_claim)]
+        tmp = f"{self.path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
+def tune_mixed_cached(cache: TuningCache, pset: PlanSet, frames, Dmax: int, llr, llr_off, info, info_off, pm,
+                      status, stream=None, order=None, device: str | None = None, tuner=None):
+    """scs_tune_mixed through a TuningCache: a known key sets the stored shape
+    on the set (no device work); otherwise the native autotuner runs on this
+    batch and its result is stored.  Returns (warps per block, frames per
+    claim, True if it came from the cache).  ``tuner`` replaces
+    scs_tune_mixed (same arguments), e.g. in tests without a GPU."""
+    if device is None:
+        import torch
+
+        device = torch.cuda.get_device_name(torch.cuda.current_device())
+    key = tuning_key(pset, Dmax, device)
+    hit = cache.lookup(key)
+    if hit is not None:
+        polar_plan_set_tuning(pset, *hit)
+        return hit[0], hit[1], True
+    w, c = (tuner or scs_tune_mixed)(pset, frames, Dmax, llr, llr_off, info, info_off, pm, status, stream=stream,
+                                     order=order)
+    polar_plan_set_tuning(pset, w, c)
+    cache.store(key, w, c)
+    return w, c, False
+
+
+def save_scales(path: str, scales) -> None:
+    """Write learned per-stage scales (float32) to a JSON file; every float32
+    value is exact as a JSON number."""
+    import json
+
+    sc = np.ascontiguousarray(scales, dtype=np.float32)
+    with open(path, "w") as f:
+        json.dump({"stages": int(sc.size), "scales": [float(x) for x in sc]}, f)
+
+
+def load_scales(path: str) -> np.ndarray:
+    """Read scales written by save_scales (float32, one per stage)."""
+    import json
+
+    with open(path) as f:
+        data = json.load(f)
+    sc = np.asarray(data["scales"], dtype=np.float32)
+    if sc.size != int(data["stages"]):
+        raise ValueError(f"{path}: {sc.size} scales for {data['stages']} stages")
+    return sc
 
 
 def polar_mixed_split_order(pset: PlanSet, frames_host: np.ndarray):

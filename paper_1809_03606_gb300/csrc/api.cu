@@ -338,6 +338,25 @@ extern "C" int scs_tune_mixed(polar_plan_set *set, const int32_t *d_frames, cons
     return 0;
 }
 
+extern "C" int polar_plan_set_tuning(polar_plan_set *set, int warps_per_block, int frames_per_claim) {
+    if (!set) return POLAR_EINVAL;
+    const bool clear = warps_per_block == 0 && frames_per_claim == 0;
+    const bool wpb_ok = warps_per_block == 1 || warps_per_block == 2 || warps_per_block == 4;
+    if (!clear && (!wpb_ok || frames_per_claim < 1 || frames_per_claim > 1024)) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(set->mu);
+    set->tuned_wpb = warps_per_block;
+    set->tuned_chunk = frames_per_claim;
+    return 0;
+}
+
+extern "C" int polar_plan_set_get_tuning(const polar_plan_set *set, int *warps_per_block, int *frames_per_claim) {
+    if (!set || !warps_per_block || !frames_per_claim) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(set->mu);
+    *warps_per_block = set->tuned_wpb;
+    *frames_per_claim = set->tuned_chunk;
+    return 0;
+}
+
 template <typename T>
 static int gsc_call(const polar_plan *p, const T *d_llr, const uint32_t *d_u, int B, const T *d_scales, T *d_loss,
                     T *d_grad_scales, T *d_grad_llr, T *d_leaf, void *stream) {
